@@ -42,6 +42,14 @@ int orc_num_threads(void) {
 #endif
 }
 
+/* Compensated (Neumaier) summation step. */
+static void neumaier_add(double *sum, double *comp, double x) {
+  double t = *sum + x;
+  if (fabs(*sum) >= fabs(x)) *comp += (*sum - t) + x;
+  else *comp += (x - t) + *sum;
+  *sum = t;
+}
+
 /* ------------------------------------------------------------------ lattice */
 
 /* d2v72 (Sec. 2.4): 12 directions phi_d = d pi/6 (roots of sin 6 phi) times the
@@ -300,21 +308,33 @@ static void ensure_tables(void) {
  * function is taken with the NPHI-point trapezoid rule, which is exact to
  * round-off for |u| <= 0.95. */
 void orc_eq_moments(int edf, double theta, double ux, double uy, double z, double M[36]) {
+  orc_eq_moments_ne(edf, -1.0, -1.0, theta, ux, uy, z, M);
+}
+
+/* As orc_eq_moments, but with the radial factors of degree 1 and 2 written
+ * through Eq. (25): g_2 theta^2 = n / (2 pi) and 2! g_3 theta^3 = eps / (2 pi),
+ * with the given n and eps (ignored when negative). The collision then
+ * reproduces the cell's own n and eps exactly, up to rounding. */
+void orc_eq_moments_ne(int edf, double n, double eps, double theta, double ux, double uy, double z,
+                       double M[36]) {
   ensure_tables();
   double gamma = 1.0 / sqrt(1.0 - ux * ux - uy * uy);
-  double ang[36];
-  for (int a = 0; a < 36; ++a) ang[a] = 0.0;
+  double ang[36], comp[36];
+  for (int a = 0; a < 36; ++a) ang[a] = comp[a] = 0.0;
   for (int j = 0; j < NPHI; ++j) {
     double r = 1.0 / (gamma * (1.0 - ux * trap_cos[j] - uy * trap_sin[j]));
     double rp[7];
     rp[0] = 1.0;
     for (int e = 1; e <= 6; ++e) rp[e] = rp[e - 1] * r;
-    for (int a = 0; a < 36; ++a) ang[a] += trap_trig[a][j] * rp[basis_n[a] + 1];
+    for (int a = 0; a < 36; ++a) neumaier_add(&ang[a], &comp[a], trap_trig[a][j] * rp[basis_n[a] + 1]);
   }
   for (int a = 0; a < 36; ++a) {
     double fact = 1.0;
     for (int i = 2; i <= basis_n[a]; ++i) fact *= i;
-    M[a] = fact * orc_g(edf, basis_n[a] + 1, z) * pow(theta, basis_n[a] + 1) * (2.0 * PI / NPHI) * ang[a];
+    double radial = fact * orc_g(edf, basis_n[a] + 1, z) * pow(theta, basis_n[a] + 1);
+    if (basis_n[a] == 1 && n >= 0.0) radial = n / (2.0 * PI);
+    if (basis_n[a] == 2 && eps >= 0.0) radial = eps / (2.0 * PI);
+    M[a] = radial * (2.0 * PI / NPHI) * (ang[a] + comp[a]);
   }
 }
 
@@ -322,6 +342,7 @@ void orc_eq_moments(int edf, double theta, double ux, double uy, double z, doubl
 
 /* Gram matrix of the basis p^n trig(k phi) under the d2v72 weights, its
  * Cholesky factor and the basis values at the 72 nodes, per EDF (built once). */
+static double gram_G[3][36][36];
 static double gram_L[3][36][36];
 static double node_phi[3][72][36];
 static int gram_ready[3];
@@ -344,9 +365,12 @@ static void ensure_gram(int edf) {
       double G[36][36];
       for (int a = 0; a < 36; ++a)
         for (int b = 0; b < 36; ++b) {
-          double sum = 0.0;
-          for (int q = 0; q < 72; ++q) sum += w[q % 6] * node_phi[edf][q][a] * node_phi[edf][q][b];
-          G[a][b] = sum;
+          /* compensated: G is used for every cell, so its rounding must not bias the
+           * equilibrium's moments */
+          double sum = 0.0, comp = 0.0;
+          for (int q = 0; q < 72; ++q) neumaier_add(&sum, &comp, w[q % 6] * node_phi[edf][q][a] * node_phi[edf][q][b]);
+          G[a][b] = sum + comp;
+          gram_G[edf][a][b] = sum + comp;
         }
       /* Cholesky G = L L^T */
       double (*L)[36] = gram_L[edf];
@@ -366,6 +390,21 @@ static void ensure_gram(int edf) {
   }
 }
 
+/* Solve L L^T x = b (forward then backward substitution). */
+static void cholesky_solve(const double (*L)[36], const double b[36], double x[36]) {
+  double y[36];
+  for (int i = 0; i < 36; ++i) {
+    double s = b[i];
+    for (int k = 0; k < i; ++k) s -= L[i][k] * y[k];
+    y[i] = s / L[i][i];
+  }
+  for (int i = 35; i >= 0; --i) {
+    double s = y[i];
+    for (int k = i + 1; k < 36; ++k) s -= L[k][i] * x[k];
+    x[i] = s / L[i][i];
+  }
+}
+
 /* Eqs. (10)-(11) read as an orthogonal projection (the 36 relativistic
  * polynomials P^{i..}, P^{i..0} of degree <= 5 span the same space as
  * p^n {cos, sin}(k phi), 0 <= k <= n <= 5, and are orthonormal under
@@ -373,26 +412,34 @@ static void ensure_gram(int edf) {
  * continuous moments M_b of f^eq. The quadrature is exact to degree 10, so the
  * discrete f^eq reproduces every moment of degree <= 5. */
 void orc_feq(int edf, double theta, double ux, double uy, double z, double feq[72]) {
+  orc_feq_ne(edf, -1.0, -1.0, theta, ux, uy, z, feq);
+}
+
+void orc_feq_ne(int edf, double n, double eps, double theta, double ux, double uy, double z,
+                double feq[72]) {
   ensure_gram(edf);
-  double M[36], y[36], c[36];
-  orc_eq_moments(edf, theta, ux, uy, z, M);
+  double M[36], c[36], r[36], dc[36];
+  orc_eq_moments_ne(edf, n, eps, theta, ux, uy, z, M);
   const double (*L)[36] = (const double (*)[36])gram_L[edf];
+  const double (*G)[36] = (const double (*)[36])gram_G[edf];
+  /* G c = M by Cholesky, then one step of iterative refinement (r = M - G c,
+   * G dc = r, c += dc): the refined c reproduces the moments M to rounding, so
+   * the discrete equilibrium carries no systematic defect in N^0, T^{mu 0}. */
+  cholesky_solve(L, M, c);
   for (int i = 0; i < 36; ++i) {
-    double s = M[i];
-    for (int k = 0; k < i; ++k) s -= L[i][k] * y[k];
-    y[i] = s / L[i][i];
+    double sum = M[i];
+    for (int k = 0; k < 36; ++k) sum -= G[i][k] * c[k];
+    r[i] = sum;
   }
-  for (int i = 35; i >= 0; --i) {
-    double s = y[i];
-    for (int k = i + 1; k < 36; ++k) s -= L[k][i] * c[k];
-    c[i] = s / L[i][i];
-  }
+  cholesky_solve(L, r, dc);
+  for (int i = 0; i < 36; ++i) c[i] += dc[i];
   double w[6];
   orc_lattice(edf, NULL, w, NULL, NULL);
   for (int q = 0; q < 72; ++q) {
-    double v = 0.0;
-    for (int a = 0; a < 36; ++a) v += node_phi[edf][q][a] * c[a];
-    feq[q] = w[q % 6] * v;
+    /* compensated: the terms cancel strongly on the outer shells */
+    double v = 0.0, cv = 0.0;
+    for (int a = 0; a < 36; ++a) neumaier_add(&v, &cv, node_phi[edf][q][a] * c[a]);
+    feq[q] = w[q % 6] * (v + cv);
   }
 }
 
@@ -446,20 +493,30 @@ double orc_expansion_at(int edf, int order, double theta, double ux, double uy, 
   return omega * v;
 }
 
-/* N^mu = sum_i f_i p^mu_i and T^{mu nu} = sum_i f_i p^mu_i p^nu_i, Eqs. (20), (22). */
+/* N^mu = sum_i f_i p^mu_i and T^{mu nu} = sum_i f_i p^mu_i p^nu_i, Eqs. (20), (22).
+ * The sums are compensated (Neumaier): the momentum components cancel between
+ * opposite directions, and a plain sum would leave an error of one unit of the
+ * energy density in them, i.e. an error in u that does not shrink with u. */
 void orc_moments72(int edf, const double f[72], double N[3], double T[6]) {
   double p[6], cphi[12], sphi[12];
   orc_lattice(edf, p, NULL, cphi, sphi);
-  for (int i = 0; i < 3; ++i) N[i] = 0.0;
-  for (int i = 0; i < 6; ++i) T[i] = 0.0;
+  double sN[3] = {0, 0, 0}, cN[3] = {0, 0, 0}, sT[6] = {0, 0, 0, 0, 0, 0}, cT[6] = {0, 0, 0, 0, 0, 0};
   for (int d = 0; d < 12; ++d)
     for (int s = 0; s < 6; ++s) {
       double v = f[6 * d + s];
       double p0 = p[s], px = p[s] * cphi[d], py = p[s] * sphi[d];
-      N[0] += v * p0; N[1] += v * px; N[2] += v * py;
-      T[0] += v * p0 * p0; T[1] += v * p0 * px; T[2] += v * p0 * py;
-      T[3] += v * px * px; T[4] += v * px * py; T[5] += v * py * py;
+      neumaier_add(&sN[0], &cN[0], v * p0);
+      neumaier_add(&sN[1], &cN[1], v * px);
+      neumaier_add(&sN[2], &cN[2], v * py);
+      neumaier_add(&sT[0], &cT[0], v * p0 * p0);
+      neumaier_add(&sT[1], &cT[1], v * p0 * px);
+      neumaier_add(&sT[2], &cT[2], v * p0 * py);
+      neumaier_add(&sT[3], &cT[3], v * px * px);
+      neumaier_add(&sT[4], &cT[4], v * px * py);
+      neumaier_add(&sT[5], &cT[5], v * py * py);
     }
+  for (int i = 0; i < 3; ++i) N[i] = sN[i] + cN[i];
+  for (int i = 0; i < 6; ++i) T[i] = sT[i] + cT[i];
 }
 
 /* ------------------------------------------------------- streaming and BCs */
@@ -590,7 +647,7 @@ int orc_step(const orc_domain *D, const double *f_in, const double *macro_in, do
   }
   double cphi[12], sphi[12];
   orc_lattice(edf, NULL, NULL, cphi, sphi);
-#pragma omp parallel for reduction(| : st) schedule(static)
+#pragma omp parallel for collapse(2) reduction(| : st) schedule(static)
   for (int y = 0; y < ny; ++y) {
     for (int x = 0; x < nx; ++x) {
       double f[72], feq[72], N[3], T[6], m[6];
@@ -602,7 +659,11 @@ int orc_step(const orc_domain *D, const double *f_in, const double *macro_in, do
       if (cs & ORC_E_NONPHYSICAL) {
         for (int q = 0; q < 72; ++q) f_out[q * plane + i] = f[q];
       } else {
-        orc_feq(edf, m[1], m[2], m[3], m[4], feq);
+        /* degree-1/2 moments from the cell's n and eps (Eq. 25); a clamped BE
+         * state uses the equilibrium's own eps = 4 pi theta^3 g_3(z_c) */
+        double eps_eq = (cs & ORC_W_CLAMPED_FUGACITY)
+                            ? 4.0 * PI * m[1] * m[1] * m[1] * orc_g(edf, 3, m[4]) : m[5];
+        orc_feq_ne(edf, m[0], eps_eq, m[1], m[2], m[3], m[4], feq);
         double gamma = 1.0 / sqrt(1.0 - m[2] * m[2] - m[3] * m[3]);
         for (int d = 0; d < 12; ++d) {
           double om = gamma * (1.0 - (cphi[d] * m[2] + sphi[d] * m[3])) / D->tau;
@@ -629,7 +690,7 @@ int orc_init(const orc_domain *D, int kind, const double *a, const double *theta
   int nx = D->nx, ny = D->ny, edf = D->edf, st = 0;
   size_t plane = (size_t)nx * ny;
   ensure_gram(edf);
-#pragma omp parallel for reduction(| : st) schedule(static)
+#pragma omp parallel for collapse(2) reduction(| : st) schedule(static)
   for (int y = 0; y < ny; ++y)
     for (int x = 0; x < nx; ++x) {
       size_t i = (size_t)y * nx + x;
@@ -667,7 +728,7 @@ int orc_fields(const orc_domain *D, const double *f_in, const double *macro_in, 
     c.ghost_y = (double *)malloc(sizeof(double) * 2 * nx * 72);
     st |= build_wall_ghosts(D, macro_in, c.ghost_x, c.ghost_y);
   }
-#pragma omp parallel for reduction(| : st) schedule(static)
+#pragma omp parallel for collapse(2) reduction(| : st) schedule(static)
   for (int y = 0; y < ny; ++y)
     for (int x = 0; x < nx; ++x) {
       double f[72], N[3], T[6], m[6];

@@ -63,11 +63,20 @@ int orc_z_from_n_theta(int edf, double n, double theta, double *z);
  * of orc_basis_index, by trapezoidal angular integration (Appendix). */
 void orc_eq_moments(int edf, double theta, double ux, double uy, double z, double M[36]);
 
+/* Same with the degree-1 and degree-2 radial factors taken from n and eps via
+ * Eq. (25) (n/(2 pi) and eps/(2 pi)); a negative n or eps is ignored. */
+void orc_eq_moments_ne(int edf, double n, double eps, double theta, double ux, double uy, double z,
+                       double M[36]);
+
 /* Basis function list: for a in 0..35, n[a], k[a], c[a] (c = 0 cos, 1 sin). */
 void orc_basis(int n[36], int k[36], int c[36]);
 
 /* Discrete fifth-order equilibrium f^eq_q (projection onto degree <= 5), Eqs. (10)-(11). */
 void orc_feq(int edf, double theta, double ux, double uy, double z, double feq[72]);
+
+/* Same with n and eps fixing the degree-1 and degree-2 moments (Eq. 25). */
+void orc_feq_ne(int edf, double n, double eps, double theta, double ux, double uy, double z,
+                double feq[72]);
 
 /* Value of the order-N expansion (N = 1..5) at an arbitrary momentum (Fig. 1). */
 double orc_expansion_at(int edf, int order, double theta, double ux, double uy, double z,
