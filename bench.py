@@ -1,0 +1,365 @@
+#!/usr/bin/env python
+"""Throughput benchmark: lattice updates per second of the fused stream-collide
+step on GB300, mixed-precision batched form (headline) against the plain FP64
+form, with the roofline of the dominant kernel and the FP64 CPU oracle timed on
+the host cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+Workload (headline): 256 periodic Taylor-Green domains of uneven size (sides
+uniform in 32..512, seed 20260101), MJ fifth-order equilibrium, tau swept
+0.55..2.0, amplitudes 0.005..0.05 c, FP32 populations, one launch per step over
+a tile work list, autotuned grid, steps replayed from a CUDA graph. Under
+torchrun each rank runs its own independently seeded batch (weak scaling, no
+data-path collective); rank 0 prints one JSON line.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_1709_09073_gb300 import workloads as W  # noqa: E402
+
+METRIC = "lattice updates/s (MLUPS) FP64 vs mixed+batched on 1 GB300; % roofline"
+UNIT = "MLUPS"
+BYTES_PER_CELL = {0: 1152, 1: 576, 2: 288, 3: 288}   # 2 x 72 x element size
+STORAGE_NAME = {0: "f64", 1: "f32", 2: "bf16dev", 3: "f16dev"}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+# FP64 pipe: 2 FMA per clock per SM on GB300 (1.19 TFLOP/s measured with an FMA
+# chain at 2070 MHz); the ALU roofline uses 152 SMs x 2 FMA x 2 flop x SM clock.
+FP64_FLOP_PER_CLK_SM = 4.0
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples taken during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[3:7]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def gpu_index(local):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    ids = [v for v in vis.split(",") if v.strip()]
+    if ids and ids[min(local, len(ids) - 1)].strip().isdigit():
+        return int(ids[min(local, len(ids) - 1)])
+    return local
+
+
+def timed_steps(sim, steps, torch):
+    """Device time (s) of `steps` steps with CUDA events on the handle's stream."""
+    s = sim.stream
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    sim.step(steps)
+    e1.record(s)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def barrier_max(t, world, torch):
+    if world == 1:
+        return t
+    import torch.distributed as dist
+    v = torch.tensor([t], dtype=torch.float64, device="cuda")
+    dist.all_reduce(v, op=dist.ReduceOp.MAX)
+    return float(v.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def traffic_record(kernel):
+    """DRAM bytes per cell of `kernel` from the committed ncu summary, if current."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+        return d.get(kernel)
+    except ValueError:
+        return None
+
+
+def run_native(args):
+    import torch
+    from paper_1709_09073_gb300 import build, rlbm
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    build.build()
+    rlbm.load()
+    wl = W.batched_taylor_green(seed=20260101 + rank)
+    cells = wl.cells
+    storage = rlbm.RLBM_F32
+    sim, st0 = rlbm.from_workload(wl, storage=storage)
+    grid = sim.tune(3)
+    sim.step(args.warmup)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(gpu_index(local))
+    barrier(world)
+    sampler.start()
+    t = timed_steps(sim, args.steps, torch)
+    clocks = sampler.stop()
+    barrier(world)
+    t = barrier_max(t, world, torch)
+    status = sim.sync_status()
+    value = cells * world * args.steps / t / 1e6
+    per_launch = t / args.steps
+    bpc = BYTES_PER_CELL[storage]
+    achieved = bpc * cells / per_launch / 1e9
+    hbm_peak, peak_kind = peaks()
+    tr = traffic_record("k_step_mixed_f32_mj")
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(achieved / hbm_peak, 4),
+                "traffic": round(tr * cells) if tr else None,
+                "peak_source": peak_kind, "kernel": "k_step_mixed<MJ, F32>",
+                "algorithmic_bytes_per_cell": bpc}
+    launches = sim.last_step_info()[1]
+
+    # end to end through the public API with host buffers: fields uploaded from
+    # pinned host memory, every step followed by a status read-back, fields
+    # read back to pinned host memory at the end
+    pinned = []
+    for s in wl.init:
+        pinned.append([torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+                       for x in (s.a, s.theta, s.ux, s.uy)])
+    e2e_steps = max(1, args.steps // 4)
+    out_host = [[torch.empty((d.ny, d.nx), dtype=torch.float64).pin_memory() for _ in range(5)]
+                for d in wl.domains]
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i, (d, s) in enumerate(zip(wl.domains, wl.init)):
+        dev = [x.to("cuda", non_blocking=True) for x in pinned[i]]
+        sim.init(i, W.InitialState(s.kind, *dev))
+    for _ in range(e2e_steps):
+        sim.step(1)
+        sim.sync_status()
+    for i in range(len(wl.domains)):
+        outs = sim.moments(i, on_device=True)
+        for o, h in zip(outs, out_host[i]):
+            h.copy_(o, non_blocking=True)
+    torch.cuda.synchronize()
+    te = time.perf_counter() - t0
+    te = barrier_max(te, world, torch)
+    h2d = 4 * 8 * cells
+    d2h = 5 * 8 * cells + 4 * e2e_steps
+    e2e = {"value": round(cells * world * e2e_steps / te / 1e6, 2), "unit": UNIT,
+           "h2d_bytes_per_step": int(h2d / e2e_steps), "d2h_bytes_per_step": int(d2h / e2e_steps),
+           "steps": e2e_steps, "what": "upload fields -> rlbm_init -> (rlbm_step(1) + status read) x K -> "
+                                       "rlbm_moments to pinned host"}
+    sim.close()
+    del sim
+
+    # the plain FP64 form on the same workload (the comparison the metric names)
+    fp64 = None
+    if not args.no_fp64:
+        sim64, _ = rlbm.from_workload(wl, storage=rlbm.RLBM_F64)
+        sim64.tune(1)
+        sim64.step(max(1, args.warmup // 10))
+        k64 = max(2, args.steps // 20)
+        barrier(world)
+        t64 = barrier_max(timed_steps(sim64, k64, torch), world, torch)
+        v64 = cells * world * k64 / t64 / 1e6
+        flops_per_cell = FP64_FLOPS_PER_CELL
+        clk = (clocks or {}).get("sm_mhz") or 2070.0
+        alu_peak = 152 * FP64_FLOP_PER_CLK_SM * clk * 1e6 / 1e12
+        ach = flops_per_cell * cells / (t64 / k64) / 1e12
+        fp64 = {"value": round(v64, 2), "unit": UNIT, "steps": k64,
+                "ms_per_step": round(t64 / k64 * 1e3, 3),
+                "roofline": {"bound": "alu", "achieved": round(ach, 4), "peak": round(alu_peak, 4),
+                             "unit": "TFLOP/s (FP64)", "frac": round(ach / alu_peak, 4),
+                             "flops_per_cell": flops_per_cell,
+                             "peak_source": "152 SMs x 2 FP64 FMA/clk x median SM clock"},
+                "hbm_achieved_gbs": round(1152 * cells / (t64 / k64) / 1e9, 1)}
+        sim64.close()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline(wl, budget_s=args.cpu_seconds)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": round(t / args.steps * 1e3, 4), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 totals and Landau solve)",
+                "data": "synthetic",
+                "config": {"workload": wl.name, "domains": len(wl.domains), "cells_per_gpu": cells,
+                           "sides": "uniform 32..512 (seed 20260101 + rank)", "tau": "0.55..2.0",
+                           "u0": "0.005..0.05", "edf": "MJ", "order": 5, "storage": "f32",
+                           "grid": grid, "l2": "inputs larger than L2 (%.1f GB of populations)"
+                           % (2 * 288 * cells / 1e9), "parallelism": "independent domains per GPU"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clocks, "fp64": fp64, "status": status}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# FP64 operations per cell update of the plain kernel (k_step_f64<MJ>), FMA = 2,
+# counted from the instruction mix that ncu reports for one launch (see
+# profiles/); used for the FP64 ALU roofline of the plain form.
+FP64_FLOPS_PER_CELL = 2900
+
+
+def cpu_baseline(wl, budget_s=15.0):
+    """The FP64 oracle, as it stands, on the host cores: whole domains of the
+    workload, one step each, until the time budget is used."""
+    from oracle import oracle as O
+    O.build()
+    done_cells, t_used, ndom = 0, 0.0, 0
+    for d, s in zip(wl.domains, wl.init):
+        dom = O.domain(d.nx, d.ny, d.tau, d.edf, d.bc, d.t_wall)
+        f, macro, _ = O.init(dom, s.kind, s.a, s.theta, s.ux, s.uy)
+        t0 = time.perf_counter()
+        O.step(dom, f, macro)
+        t_used += time.perf_counter() - t0
+        done_cells += d.nx * d.ny
+        ndom += 1
+        if t_used > budget_s:
+            break
+    return {"value": round(done_cells / t_used / 1e6, 4), "unit": UNIT, "cores": O.num_threads(),
+            "kind": "oracle",
+            "sample": "1 step of each of the first %d domains (%d cells) of the workload" % (ndom, done_cells)}
+
+
+def run_reference(args):
+    """The oracle as the reference arm: same metric, bounded sample per step."""
+    world, rank, local = dist_env()
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    O.build()
+    wl = W.batched_taylor_green(seed=20260101)
+    # one bounded sample: the first domains up to ~0.6 M cells, one step each per "step"
+    sample, cells = [], 0
+    for d, s in zip(wl.domains, wl.init):
+        sample.append((d, s))
+        cells += d.nx * d.ny
+        if cells > 600_000:
+            break
+    states = []
+    for d, s in sample:
+        dom = O.domain(d.nx, d.ny, d.tau, d.edf, d.bc, d.t_wall)
+        f, macro, _ = O.init(dom, s.kind, s.a, s.theta, s.ux, s.uy)
+        states.append([dom, f, macro])
+
+    def one_step():
+        for stt in states:
+            f, mo, _ = O.step(stt[0], stt[1], stt[2])
+            stt[1], stt[2] = f, mo[[0, 2, 3]].copy()
+
+    for _ in range(args.warmup):
+        one_step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one_step()
+    t = time.perf_counter() - t0
+    value = cells * args.steps / t / 1e6
+    sample_txt = "first %d domains of %s (%d cells), full step each" % (len(sample), wl.name, cells)
+    line = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t / args.steps * 1e3, 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": wl.name, "sample": sample_txt},
+            "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": O.num_threads(),
+                             "kind": "oracle", "sample": sample_txt},
+            "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

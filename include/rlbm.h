@@ -1,0 +1,167 @@
+/*
+ * rlbm.h -- C ABI of the GB300 (sm_103a) implementation of the fully
+ * dissipative two-dimensional ultra-relativistic lattice Boltzmann method of
+ * Coelho, Mendoza, Doria and Herrmann, arXiv:1709.09073.
+ *
+ * The library advances populations f_i on the d2v72 quadrature (12 directions
+ * phi_d = d pi/6 times 6 energy shells, Sec. 2.4) with the fused per-cell
+ * update of the paper: bilinear interpolated pull-streaming (Eqs. 17-18),
+ * moments N^mu and T^{mu nu} (Eqs. 20, 22), the Landau-frame eigenproblem
+ * T^a_b U^b = eps U^a (Eq. 21), temperature and fugacity (Eqs. 24-25), the
+ * fifth-order expansion of the Maxwell-Juttner, Fermi-Dirac or Bose-Einstein
+ * equilibrium (Eqs. 10-11, Appendix) and Anderson-Witting relaxation (Eq. 3).
+ *
+ * Conventions shared by every call
+ *  - Units: delta t = delta x = c = k_B = 1; theta = T/T_0 (Sec. 2.3).
+ *  - Population index q = 6 d + s: direction d = 0..11 (phi_d = d pi/6,
+ *    counter-clockwise from +x), shell s = 0..5 (ascending momentum).
+ *  - Macroscopic field arrays are row-major [ny][nx] FP64 (index y*nx + x),
+ *    on the host or on the device as the `on_device` argument says.
+ *  - Device memory: the caller allocates ONE workspace of
+ *    rlbm_workspace_bytes(config) bytes (256-byte aligned) and keeps it alive
+ *    until rlbm_destroy; the library allocates no device memory of its own.
+ *    The handle (host memory) and a captured CUDA graph belong to the library.
+ *  - Streams: every call is ordered on config->cuda_stream (a cudaStream_t;
+ *    NULL = the legacy default stream). rlbm_step is asynchronous; calls that
+ *    return data to host memory synchronise that stream before returning.
+ *  - Return codes: 0 = success, > 0 = warning bits (the call completed),
+ *    < 0 = error (nothing was done, or the device state is unspecified for
+ *    RLBM_E_CUDA). rlbm_status_string() describes any code.
+ *  - Threads: a handle must not be used by two host threads at once.
+ */
+#ifndef RLBM_H
+#define RLBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rlbm_ctx *rlbm_handle;
+
+/* Equilibrium distribution, Eq. (7): xi = 0 (MJ), 1 (FD), -1 (BE). Every
+ * domain of one handle uses the same EDF. */
+typedef enum { RLBM_MJ = 0, RLBM_FD = 1, RLBM_BE = 2 } rlbm_edf;
+
+/* Storage of the populations in HBM.
+ *  RLBM_F64      FP64 populations, FP64 arithmetic throughout (the plain method).
+ *  RLBM_F32      FP32 populations; FP32 streaming, equilibrium and relaxation;
+ *                moments and Landau solve in FP64-class precision.
+ *  RLBM_BF16DEV, RLBM_F16DEV, RLBM_F32DEV
+ *                relative deviations h = (f / f_ref - 1) / scale from the rest
+ *                equilibrium f_ref(ref_n, ref_theta) of each domain, stored in
+ *                BF16, FP16 or FP32; arithmetic as for RLBM_F32. */
+typedef enum { RLBM_F64 = 0, RLBM_F32 = 1, RLBM_BF16DEV = 2, RLBM_F16DEV = 3, RLBM_F32DEV = 4 } rlbm_storage;
+
+/* Boundary condition of one side (one ghost layer; Sec. 3):
+ *  RLBM_PERIODIC       wrap-around (must be set on both sides of an axis);
+ *  RLBM_ZERO_GRADIENT  the ghost copies the adjacent edge cell (open ends);
+ *  RLBM_FIXED_T_WALL   the ghost holds f^eq(n_b, u_b, theta_wall) with n_b, u_b
+ *                      the pre-collision state of the adjacent fluid cell at the
+ *                      current time (zeroth-order extrapolation, Sec. 3.3).
+ *  At a corner outside both axes an x-side wall takes precedence over a y-side wall. */
+typedef enum { RLBM_PERIODIC = 0, RLBM_ZERO_GRADIENT = 1, RLBM_FIXED_T_WALL = 2 } rlbm_bc;
+
+/* Meaning of the first field given to rlbm_init. */
+typedef enum { RLBM_INIT_N_THETA = 0, RLBM_INIT_Z_THETA = 1 } rlbm_init_kind;
+
+typedef struct {
+  int nx, ny;                 /* lattice size, >= 1 each */
+  double tau;                 /* relaxation time (Eq. 3), > 0 */
+  int bc_xlo, bc_xhi, bc_ylo, bc_yhi;                /* rlbm_bc */
+  double t_wall_xlo, t_wall_xhi, t_wall_ylo, t_wall_yhi; /* wall theta, if a wall */
+  double ref_n, ref_theta;    /* reference rest equilibrium of the mixed storages */
+  double scale;               /* deviation scale of the *DEV storages (> 0) */
+} rlbm_domain;
+
+typedef struct {
+  int ndomains;               /* >= 1 independent domains, advanced together */
+  const rlbm_domain *domains; /* host array of ndomains descriptors (copied) */
+  int edf;                    /* rlbm_edf */
+  int storage;                /* rlbm_storage */
+  int order;                  /* expansion order of Eq. (10); only 5 is supported */
+  void *device_buffer;        /* caller-owned workspace, rlbm_workspace_bytes() */
+  size_t buffer_bytes;
+  void *cuda_stream;          /* cudaStream_t or NULL */
+} rlbm_config;
+
+/* Status codes. Warnings are bits that may be OR-ed together. */
+#define RLBM_OK 0
+#define RLBM_W_LANDAU_MAXITER 1     /* Landau solve hit its iteration cap in some cell */
+#define RLBM_W_CLAMPED_FUGACITY 2   /* BE state beyond z_c clamped to z_c (n kept) */
+#define RLBM_W_NONPHYSICAL 4        /* some cell had |u|>=1, n<=0, eps<=0 or a non-finite
+                                       moment; it was streamed but not relaxed */
+#define RLBM_W_ZSOLVE 8             /* fugacity solve (FD/BE) did not converge in some cell */
+#define RLBM_E_ARG (-1)             /* invalid argument */
+#define RLBM_E_CUDA (-2)            /* a CUDA call failed */
+#define RLBM_E_STATE (-3)           /* call out of order (e.g. step before init) */
+#define RLBM_E_UNSUPPORTED (-4)     /* valid but unsupported combination */
+#define RLBM_E_NOBUFFER (-5)        /* device buffer missing, misaligned or too small */
+
+/* Bytes of device workspace the configuration needs (0 if the config is invalid).
+ * Holds two halo-padded population copies, the device descriptor and tile
+ * tables, a status word and a host-transfer staging area. */
+size_t rlbm_workspace_bytes(const rlbm_config *config);
+
+/* Create a handle over the caller's workspace. Copies the descriptors; uploads
+ * the tables; does not initialise populations. *out = NULL on error. */
+int rlbm_create(const rlbm_config *config, rlbm_handle *out);
+
+/* Set domain `domain` to the equilibrium f = f^eq of the given fields (time 0;
+ * an equilibrium is its own post-collision state). kind = RLBM_INIT_N_THETA:
+ * a = n; RLBM_INIT_Z_THETA: a = fugacity z (MJ: z = n / (2 pi theta^2), Eq. 25).
+ * Fields are [ny][nx] FP64 on host (on_device = 0) or device (1). Every domain
+ * must be initialised before the first rlbm_step. Returns warning bits of the
+ * fugacity solve, or an error. */
+int rlbm_init(rlbm_handle h, int domain, int kind, const double *a, const double *theta,
+              const double *ux, const double *uy, int on_device);
+
+/* Advance every domain by nsteps >= 0 fused stream-collide steps (Eqs. 3,
+ * 17-18), asynchronously on the handle's stream (replayed from a captured CUDA
+ * graph). Returns RLBM_OK or an error; per-cell warnings accumulate on the
+ * device and are read by rlbm_sync_status. */
+int rlbm_step(rlbm_handle h, int nsteps);
+
+/* Macroscopic fields of domain `domain`: streamed = 1 gives the state of the
+ * populations after streaming the stored post-collision populations (what the
+ * next step relaxes); streamed = 0 takes the stored populations as they are.
+ * Writes n, theta, ux, uy and, when non-NULL, z (each [ny][nx] FP64, host or
+ * device per on_device). Host outputs are complete on return. */
+int rlbm_moments(rlbm_handle h, int domain, int streamed, double *n, double *theta, double *ux,
+                 double *uy, double *z, int on_device);
+
+/* Raw state of domain `domain` for checkpoint/resume: the stored populations
+ * including the one-cell halo ring, as FP64 [72][ny+2][nx+2] (index
+ * (q*(ny+2) + y+1)*(nx+2) + x+1 for x in -1..nx, y in -1..ny), converted from
+ * the storage format. rlbm_set_populations writes them back (rounded to the
+ * storage format); a resumed run then continues bit-for-bit. */
+int rlbm_get_populations(rlbm_handle h, int domain, double *f, int on_device);
+int rlbm_set_populations(rlbm_handle h, int domain, const double *f, int on_device);
+
+/* Autotune the launch of the step kernel on the current state (left unchanged):
+ * time `repeats` launches of each candidate grid -- one block per 32 x 4 tile,
+ * or a persistent grid of k x (SM count) blocks, k in {1, 2, 3, 4, 6, 8} -- and
+ * keep the fastest for later rlbm_step calls (the captured step graphs are
+ * rebuilt). Every domain must be initialised. Returns the chosen grid size
+ * (> 0) or an error; device warnings raised while timing are discarded. */
+int rlbm_tune(rlbm_handle h, int repeats);
+
+/* Wait for the handle's stream, return the warning bits accumulated since the
+ * last call (and clear them), or RLBM_E_CUDA. */
+int rlbm_sync_status(rlbm_handle h);
+
+/* Release the handle (and its CUDA graph). The workspace stays the caller's. */
+int rlbm_destroy(rlbm_handle h);
+
+/* Static text for any status code or warning bit set. */
+const char *rlbm_status_string(int code);
+
+/* Cells x steps executed by the last rlbm_step call and kernel launches it
+ * issued (for throughput accounting). */
+int rlbm_last_step_info(rlbm_handle h, long long *cell_updates, int *kernel_launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RLBM_H */

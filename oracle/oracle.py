@@ -66,6 +66,7 @@ def lib():
         L.orc_state.argtypes = [ctypes.c_int, _D, _D, _D]
         L.orc_z_from_n_theta.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, _D]
         L.orc_eq_moments.argtypes = [ctypes.c_int] + [ctypes.c_double] * 4 + [_D]
+        L.orc_eq_moments_quad.argtypes = [ctypes.c_int] + [ctypes.c_double] * 4 + [_D]
         L.orc_basis.argtypes = [_I, _I, _I]
         L.orc_feq.argtypes = [ctypes.c_int] + [ctypes.c_double] * 4 + [_D]
         L.orc_expansion_at.argtypes = [ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 6
@@ -125,6 +126,12 @@ def basis():
 def eq_moments(edf, theta, ux, uy, z):
     M = np.zeros(36)
     lib().orc_eq_moments(edf, theta, ux, uy, z, _p(M))
+    return M
+
+
+def eq_moments_quad(edf, theta, ux, uy, z):
+    M = np.zeros(36)
+    lib().orc_eq_moments_quad(edf, theta, ux, uy, z, _p(M))
     return M
 
 

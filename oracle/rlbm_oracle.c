@@ -269,6 +269,8 @@ int orc_state(int edf, const double N[3], const double T[6], double out[6]) {
 
 /* ----------------------------------------------------- equilibrium moments */
 
+
+
 void orc_basis(int n[36], int k[36], int c[36]) {
   int a = 0;
   for (int nn = 0; nn <= 5; ++nn)
@@ -307,16 +309,126 @@ static void ensure_tables(void) {
  * (the identity before Eq. A.2). The angular integral of this smooth periodic
  * function is taken with the NPHI-point trapezoid rule, which is exact to
  * round-off for |u| <= 0.95. */
+/* The Appendix closed forms I_2^{m a b} = int d^2p/p^0 f^eq p^m (p^x)^a (p^y)^b,
+ * m + a + b <= 5, as printed (56 forms). tg2 and tg3 stand for theta^2 g_2(z)
+ * and theta^3 g_3(z); the caller may set them from n and eps through Eq. (25)
+ * (tg2 = n / (2 pi), tg3 = eps / (4 pi)). */
+static double pw(double x, int k) {
+  double r = 1.0;
+  for (int i = 0; i < k; ++i) r *= x;
+  return r;
+}
+
+static void appendix_I2(int edf, double tg2, double tg3, double th, double ux, double uy, double z,
+                        double I[6][6][6]) {
+  const double pi = PI;
+  const double u2 = ux * ux + uy * uy, gam = 1.0 / sqrt(1.0 - u2);
+  const double g1 = orc_g(edf, 1, z), g2 = orc_g(edf, 2, z), g3 = orc_g(edf, 3, z);
+  const double g4 = orc_g(edf, 4, z), g5 = orc_g(edf, 5, z), g6 = orc_g(edf, 6, z);
+  (void)g2;
+  (void)g3;
+  I[0][0][0] = 2*pi*th*g1;
+  I[1][0][0] = 2*pi*tg2*gam;
+  I[2][0][0] = 2*pi*tg3*(2 + u2)*pw(gam, 2);
+  I[3][0][0] = 6*pi*pw(th, 4)*g4*(2 + 3*u2)*pw(gam, 3);
+  I[4][0][0] = 6*pi*(8 + 24*u2 + 3*pw(u2, 2))*pw(th, 5)*g5*pw(gam, 4);
+  I[0][1][0] = 2*pi*tg2*ux*gam;
+  I[0][2][0] = 2*pi*tg3*(1 - u2 + 3*ux*ux)*pw(gam, 2);
+  I[0][3][0] = 6*pi*pw(th, 4)*g4*(3*(1 - u2)*ux + 5*pw(ux, 3))*pw(gam, 3);
+  I[0][4][0] = 6*pi*(3 + 3*pw(u2, 2) + 30*pw(ux, 2) + 35*pw(ux, 4) - 6*u2*(1 + 5*pw(ux, 2)))*pw(th, 5)*g5*pw(gam, 4);
+  I[0][0][1] = 2*pi*tg2*uy*gam;
+  I[0][0][2] = 2*pi*tg3*(1 - u2 + 3*uy*uy)*pw(gam, 2);
+  I[0][0][3] = 6*pi*pw(th, 4)*g4*(3*(1 - u2)*uy + 5*pw(uy, 3))*pw(gam, 3);
+  I[0][0][4] = 6*pi*(3 + 3*pw(u2, 2) + 30*pw(uy, 2) + 35*pw(uy, 4) - 6*u2*(1 + 5*pw(uy, 2)))*pw(th, 5)*g5*pw(gam, 4);
+  I[2][2][0] = 6*pi*(4 - 3*u2 - pw(u2, 2) + 5*pw(ux, 2)*(6 + u2))*pw(th, 5)*g5*pw(gam, 4);
+  I[1][2][0] = 6*pi*pw(th, 4)*g4*((1 - u2) + 5*ux*ux)*pw(gam, 3);
+  I[2][0][2] = 6*pi*(4 - 3*u2 - pw(u2, 2) + 5*pw(uy, 2)*(6 + u2))*pw(th, 5)*g5*pw(gam, 4);
+  I[1][0][2] = 6*pi*pw(th, 4)*g4*((1 - u2) + 5*uy*uy)*pw(gam, 3);
+  I[0][2][2] = 6*pi*((1 - u2) + 4*(1 - u2)*u2 + 35*pw(ux, 2)*pw(uy, 2))*pw(th, 5)*g5*pw(gam, 4);
+  I[0][3][1] = 30*pi*pw(th, 5)*g5*(3*(1 - u2) + 7*pw(ux, 2))*ux*uy*pw(gam, 4);
+  I[2][1][1] = 30*pi*(6 + u2)*pw(th, 5)*g5*ux*uy*pw(gam, 4);
+  I[0][1][1] = 6*pi*tg3*ux*uy*pw(gam, 2);
+  I[1][1][1] = 6*pi*pw(th, 4)*g4*(5*ux*uy)*pw(gam, 3);
+  I[1][3][0] = -30*pi*ux*(-3 + 3*u2 - 7*pw(ux, 2))*pw(th, 5)*g5*pw(gam, 4);
+  I[3][1][0] = 30*pi*(4 + 3*u2)*pw(th, 5)*ux*g5*pw(gam, 4);
+  I[1][1][0] = 6*pi*tg3*ux*pw(gam, 2);
+  I[1][0][1] = 6*pi*tg3*uy*pw(gam, 2);
+  I[0][1][3] = 30*pi*pw(th, 5)*g5*(3*(1 - u2) + 7*pw(uy, 2))*ux*uy*pw(gam, 4);
+  I[1][0][3] = -30*pi*uy*(-3 + 3*u2 - 7*pw(uy, 2))*pw(th, 5)*g5*pw(gam, 4);
+  I[1][2][1] = -30*pi*(-1 + u2 - 7*pw(ux, 2))*uy*pw(th, 5)*g5*pw(gam, 4);
+  I[2][0][1] = 6*pi*pw(th, 4)*g4*(4 + u2)*uy*pw(gam, 3);
+  I[3][0][1] = 30*pi*(4 + 3*u2)*pw(th, 5)*uy*g5*pw(gam, 4);
+  I[0][2][1] = 6*pi*pw(th, 4)*g4*((1 - u2) + 5*ux*ux)*uy*pw(gam, 3);
+  I[1][1][2] = -30*pi*(-1 + u2 - 7*pw(uy, 2))*ux*pw(th, 5)*g5*pw(gam, 4);
+  I[2][1][0] = 6*pi*pw(th, 4)*g4*(4 + u2)*ux*pw(gam, 3);
+  I[0][1][2] = 6*pi*pw(th, 4)*g4*((1 - u2) + 5*uy*uy)*ux*pw(gam, 3);
+  I[0][5][0] = 30*pi*ux*(15*pw((1 - u2), 2) + 70*pw(ux, 2)*(1 - u2) + 63*pw(ux, 4))*pw(th, 6)*g6*pw(gam, 5);
+  I[0][0][5] = 30*pi*uy*(15*pw((1 - u2), 2) + 70*pw(uy, 2)*(1 - u2) + 63*pw(uy, 4))*pw(th, 6)*g6*pw(gam, 5);
+  I[5][0][0] = 30*pi*(8 + 40*u2 + 15*pw(u2, 2))*pw(th, 6)*g6*pw(gam, 5);
+  I[2][3][0] = 30*pi*ux*(18 - 3*pw(u2, 2) + 56*pw(ux, 2) + u2*(-15 + 7*pw(ux, 2)))*pw(th, 6)*g6*pw(gam, 5);
+  I[2][0][3] = 30*pi*uy*(18 - 3*pw(u2, 2) + 56*pw(uy, 2) + u2*(-15 + 7*pw(uy, 2)))*pw(th, 6)*g6*pw(gam, 5);
+  I[0][4][1] = 90*pi*(pw((1 - u2), 2) + 14*pw(ux, 2)*(1 - u2) + 21*pw(ux, 4))*uy*pw(th, 6)*g6*pw(gam, 5);
+  I[2][2][1] = -30*pi*(-6*(1 - u2) - u2*(1 - u2) - 56*pw(ux, 2) + u2*(-7*pw(ux, 2)))*uy*pw(th, 6)*g6*pw(gam, 5);
+  I[0][1][4] = 90*pi*(pw((1 - u2), 2) + 14*pw(uy, 2)*(1 - u2) + 21*pw(uy, 4))*ux*pw(th, 6)*g6*pw(gam, 5);
+  I[0][3][2] = -30*pi*ux*(pw(ux, 2)*(-1 + 4*u2 - 63*pw(uy, 2)) + 3*(-1 + (-5 + 6*u2)*pw(uy, 2)))*pw(th, 6)*g6*pw(gam, 5);
+  I[2][1][2] = -30*pi*(-6*(1 - u2) - u2*(1 - u2) - 56*pw(uy, 2) + u2*(-7*pw(uy, 2)))*ux*pw(th, 6)*g6*pw(gam, 5);
+  I[4][1][0] = 90*pi*ux*(8 + 12*u2 + pw(u2, 2))*pw(th, 6)*g6*pw(gam, 5);
+  I[0][2][3] = -30*pi*uy*(pw(uy, 2)*(-1 + 4*u2 - 63*pw(ux, 2)) + 3*(-1 + (-5 + 6*u2)*pw(ux, 2)))*pw(th, 6)*g6*pw(gam, 5);
+  I[4][0][1] = 90*pi*uy*(8 + 12*u2 + pw(u2, 2))*pw(th, 6)*g6*pw(gam, 5);
+  I[1][4][0] = 90*pi*(pw((1 - u2), 2) + 14*pw(ux, 2)*(1 - u2) + 21*pw(ux, 4))*pw(th, 6)*g6*pw(gam, 5);
+  I[3][2][0] = -30*pi*(-4*(1 - u2) - 3*u2*(1 - u2) - 42*pw(ux, 2) + u2*(-21*pw(ux, 2)))*pw(th, 6)*g6*pw(gam, 5);
+  I[1][0][4] = 90*pi*(pw((1 - u2), 2) + 14*pw(uy, 2)*(1 - u2) + 21*pw(uy, 4))*pw(th, 6)*g6*pw(gam, 5);
+  I[3][0][2] = -30*pi*(-4*(1 - u2) - 3*u2*(1 - u2) - 42*pw(uy, 2) + u2*(-21*pw(uy, 2)))*pw(th, 6)*g6*pw(gam, 5);
+  I[1][2][2] = -30*pi*(-1 + u2 - 6*u2*(1 - u2) - 63*pw(ux, 2)*pw(uy, 2))*pw(th, 6)*g6*pw(gam, 5);
+  I[1][3][1] = -630*pi*ux*(-1 + u2 - 3*pw(ux, 2))*uy*pw(th, 6)*g6*pw(gam, 5);
+  I[3][1][1] = 315*pi*(2 + u2)*pw(th, 6)*g6*2*ux*uy*pw(gam, 5);
+  I[1][1][3] = -630*pi*uy*(-1 + u2 - 3*pw(uy, 2))*ux*pw(th, 6)*g6*pw(gam, 5);
+}
+
+/* Harmonic moments int dp dphi f^eq p^n trig(k phi) from the monomial closed
+ * forms: p^n e^{i k phi} = p^{n-k} (p^x + i p^y)^k, expanded binomially. */
+static void harmonic_from_I2(const double I[6][6][6], double M[36]) {
+  for (int a = 0; a < 36; ++a) {
+    const int n = basis_n[a], k = basis_k[a], c = basis_c[a];
+    double sum = 0.0, binom = 1.0;
+    for (int j = 0; j <= k; ++j) {
+      if (j > 0) binom = binom * (k - j + 1) / j;
+      /* i^j: real for even j (sign (-1)^(j/2)), imaginary for odd j (sign (-1)^((j-1)/2)) */
+      if ((j % 2 == 0) == (c == 0)) {
+        const double sign = ((j / 2) % 2) ? -1.0 : 1.0;
+        sum += sign * binom * I[n - k][k - j][j];
+      }
+    }
+    M[a] = sum;
+  }
+}
+
+/* The 36 equilibrium moments in the harmonic basis from the Appendix closed
+ * forms (the paper's own route to the projections, Eq. 11). */
 void orc_eq_moments(int edf, double theta, double ux, double uy, double z, double M[36]) {
   orc_eq_moments_ne(edf, -1.0, -1.0, theta, ux, uy, z, M);
 }
 
-/* As orc_eq_moments, but with the radial factors of degree 1 and 2 written
- * through Eq. (25): g_2 theta^2 = n / (2 pi) and 2! g_3 theta^3 = eps / (2 pi),
- * with the given n and eps (ignored when negative). The collision then
- * reproduces the cell's own n and eps exactly, up to rounding. */
+/* As orc_eq_moments, with the degree-1 and degree-2 radial factors written
+ * through Eq. (25) from the given n and eps (ignored when negative), so that the
+ * collision reproduces the cell's own n and eps exactly, up to rounding. */
 void orc_eq_moments_ne(int edf, double n, double eps, double theta, double ux, double uy, double z,
                        double M[36]) {
+  ensure_tables();
+  double I[6][6][6];
+  const double tg2 = n >= 0.0 ? n / (2.0 * PI) : theta * theta * orc_g(edf, 2, z);
+  const double tg3 = eps >= 0.0 ? eps / (4.0 * PI) : theta * theta * theta * orc_g(edf, 3, z);
+  memset(I, 0, sizeof(I));
+  appendix_I2(edf, tg2, tg3, theta, ux, uy, z, I);
+  harmonic_from_I2(I, M);
+}
+
+/* The same moments by direct quadrature of their definition: the radial EDF
+ * integral Gamma(n+1) g_{n+1}(z) theta^{n+1} (identity before Eq. A.2) times the
+ * angular integral of trig(k phi) / [gamma (1 - v.u)]^{n+1} with the NPHI-point
+ * trapezoid rule (exact to round-off for |u| <= 0.95). A check of the closed
+ * forms that uses nothing from them. */
+void orc_eq_moments_quad(int edf, double theta, double ux, double uy, double z, double M[36]) {
   ensure_tables();
   double gamma = 1.0 / sqrt(1.0 - ux * ux - uy * uy);
   double ang[36], comp[36];
@@ -331,10 +443,8 @@ void orc_eq_moments_ne(int edf, double n, double eps, double theta, double ux, d
   for (int a = 0; a < 36; ++a) {
     double fact = 1.0;
     for (int i = 2; i <= basis_n[a]; ++i) fact *= i;
-    double radial = fact * orc_g(edf, basis_n[a] + 1, z) * pow(theta, basis_n[a] + 1);
-    if (basis_n[a] == 1 && n >= 0.0) radial = n / (2.0 * PI);
-    if (basis_n[a] == 2 && eps >= 0.0) radial = eps / (2.0 * PI);
-    M[a] = radial * (2.0 * PI / NPHI) * (ang[a] + comp[a]);
+    M[a] = fact * orc_g(edf, basis_n[a] + 1, z) * pow(theta, basis_n[a] + 1) * (2.0 * PI / NPHI) *
+           (ang[a] + comp[a]);
   }
 }
 

@@ -60,8 +60,11 @@ int orc_state(int edf, const double N[3], const double T[6], double out[6]);
 int orc_z_from_n_theta(int edf, double n, double theta, double *z);
 
 /* The 36 equilibrium moments int dp dphi f^eq p^n {cos,sin}(k phi), basis order
- * of orc_basis_index, by trapezoidal angular integration (Appendix). */
+ * of orc_basis, from the Appendix closed forms I_2^{mnq}. */
 void orc_eq_moments(int edf, double theta, double ux, double uy, double z, double M[36]);
+
+/* The same moments by trapezoidal angular quadrature of their definition. */
+void orc_eq_moments_quad(int edf, double theta, double ux, double uy, double z, double M[36]);
 
 /* Same with the degree-1 and degree-2 radial factors taken from n and eps via
  * Eq. (25) (n/(2 pi) and eps/(2 pi)); a negative n or eps is ignored. */

@@ -1,0 +1,501 @@
+// Host side of the C ABI declared in include/rlbm.h: workspace layout, handle,
+// CUDA-graph replay of the step, host/device transfers and status handling.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "rlbm.h"
+#include "rlbm_common.h"
+#include "rlbm_launch.h"
+
+using namespace rlbm;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int kTileX = 32, kTileY = 4;
+constexpr int kChunkPairs = 16;  // a chunk graph holds 2 * kChunkPairs steps
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+size_t elem_size(int storage) {
+  switch (storage) {
+    case RLBM_F64: return 8;
+    case RLBM_F32:
+    case RLBM_F32DEV: return 4;
+    case RLBM_BF16DEV:
+    case RLBM_F16DEV: return 2;
+    default: return 0;
+  }
+}
+
+struct Layout {
+  size_t esize = 0;
+  size_t status_off = 0, doms_off = 0, tiles_off = 0, pop_off[2] = {0, 0};
+  size_t pop_elems = 0, pop_bytes = 0, total = 0;
+  std::vector<DomDev> dd;
+  std::vector<Tile> tiles;
+};
+
+bool valid_bc(int b) { return b == RLBM_PERIODIC || b == RLBM_ZERO_GRADIENT || b == RLBM_FIXED_T_WALL; }
+
+int validate(const rlbm_config* c) {
+  if (!c || c->ndomains < 1 || !c->domains) return RLBM_E_ARG;
+  if (c->edf < RLBM_MJ || c->edf > RLBM_BE) return RLBM_E_ARG;
+  if (!elem_size(c->storage)) return RLBM_E_ARG;
+  if (c->order != 5) return RLBM_E_UNSUPPORTED;
+  for (int i = 0; i < c->ndomains; ++i) {
+    const rlbm_domain& d = c->domains[i];
+    if (d.nx < 1 || d.ny < 1 || !(d.tau > 0.0)) return RLBM_E_ARG;
+    if (!valid_bc(d.bc_xlo) || !valid_bc(d.bc_xhi) || !valid_bc(d.bc_ylo) || !valid_bc(d.bc_yhi))
+      return RLBM_E_ARG;
+    if ((d.bc_xlo == RLBM_PERIODIC) != (d.bc_xhi == RLBM_PERIODIC)) return RLBM_E_ARG;
+    if ((d.bc_ylo == RLBM_PERIODIC) != (d.bc_yhi == RLBM_PERIODIC)) return RLBM_E_ARG;
+    const double tw[4] = {d.t_wall_xlo, d.t_wall_xhi, d.t_wall_ylo, d.t_wall_yhi};
+    const int bc[4] = {d.bc_xlo, d.bc_xhi, d.bc_ylo, d.bc_yhi};
+    for (int k = 0; k < 4; ++k)
+      if (bc[k] == RLBM_FIXED_T_WALL && !(tw[k] > 0.0)) return RLBM_E_ARG;
+    if (c->storage != RLBM_F64 && (!(d.scale > 0.0) || !(d.ref_n > 0.0) || !(d.ref_theta > 0.0)))
+      return RLBM_E_ARG;
+    if ((long long)d.nx * d.ny > (1LL << 31)) return RLBM_E_ARG;
+  }
+  return 0;
+}
+
+void make_layout(const rlbm_config* c, Layout& L) {
+  L.esize = elem_size(c->storage);
+  const size_t es = L.esize;
+  const int lpad = (int)(16 / es);
+  const int pitch_mult = (int)(128 / es);
+  size_t off = 0;  // elements
+  L.dd.resize(c->ndomains);
+  L.tiles.clear();
+  for (int i = 0; i < c->ndomains; ++i) {
+    const rlbm_domain& d = c->domains[i];
+    DomDev& D = L.dd[i];
+    std::memset(&D, 0, sizeof(D));
+    D.nx = d.nx;
+    D.ny = d.ny;
+    D.lpad = lpad;
+    D.pitch = (int)align_up((size_t)(lpad + d.nx + 1), (size_t)pitch_mult);
+    D.plane = (long long)D.pitch * (d.ny + 2);
+    D.off = (long long)off;
+    D.bc[0] = d.bc_xlo; D.bc[1] = d.bc_xhi; D.bc[2] = d.bc_ylo; D.bc[3] = d.bc_yhi;
+    D.inv_tau = 1.0 / d.tau;
+    D.t_wall[0] = d.t_wall_xlo; D.t_wall[1] = d.t_wall_xhi;
+    D.t_wall[2] = d.t_wall_ylo; D.t_wall[3] = d.t_wall_yhi;
+    D.ref_n = d.ref_n > 0.0 ? d.ref_n : 1.0;
+    D.ref_theta = d.ref_theta > 0.0 ? d.ref_theta : 1.0;
+    D.scale = d.scale > 0.0 ? d.scale : 1.0;
+    off = align_up(off + 72 * (size_t)D.plane, kAlign / es);
+    for (int y0 = 0; y0 < d.ny; y0 += kTileY)
+      for (int x0 = 0; x0 < d.nx; x0 += kTileX) L.tiles.push_back(Tile{i, x0, y0, 0});
+  }
+  L.pop_elems = off;
+  L.pop_bytes = align_up(off * es, kAlign);
+  size_t b = 0;
+  L.status_off = b;
+  b += kAlign;
+  L.doms_off = b;
+  b = align_up(b + sizeof(DomDev) * L.dd.size(), kAlign);
+  L.tiles_off = b;
+  b = align_up(b + sizeof(Tile) * L.tiles.size(), kAlign);
+  L.pop_off[0] = b;
+  b += L.pop_bytes;
+  L.pop_off[1] = b;
+  b += L.pop_bytes;
+  L.total = b;
+}
+
+}  // namespace
+
+struct rlbm_ctx {
+  int edf = 0, storage = 0, ndom = 0;
+  std::vector<rlbm_domain> doms;
+  Layout L;
+  char* base = nullptr;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  unsigned* d_status = nullptr;
+  DomDev* d_doms = nullptr;
+  Tile* d_tiles = nullptr;
+  void* pop[2] = {nullptr, nullptr};
+  int cur = 0;
+  std::vector<char> initialized;
+  cudaGraphExec_t pair_graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t chunk_graph[2] = {nullptr, nullptr};
+  unsigned* h_status = nullptr;  // pinned
+  long long last_updates = 0;
+  int last_launches = 0;
+  long long cells = 0;
+  int grid = 0;                  // blocks of the step kernel (0 = one per tile)
+};
+
+namespace {
+
+int cuda_fail(cudaError_t e) { return e == cudaSuccess ? RLBM_OK : RLBM_E_CUDA; }
+
+cudaError_t launch_step(rlbm_ctx* h, int from) {
+  StepArgs a;
+  a.doms = h->d_doms;
+  a.tiles = h->d_tiles;
+  a.ntiles = (int)h->L.tiles.size();
+  a.fin = h->pop[from];
+  a.fout = h->pop[1 - from];
+  a.status = h->d_status;
+  const int grid = h->grid > 0 ? h->grid : a.ntiles;
+  if (h->storage == RLBM_F64) return launch_step_f64(h->edf, a, grid, h->stream);
+  return launch_step_mixed(h->storage, h->edf, a, grid, h->stream);
+}
+
+// Capture `nsteps` (even) steps starting from copy `from` into an executable graph.
+cudaError_t capture(rlbm_ctx* h, int from, int nsteps, cudaGraphExec_t* out) {
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  cudaError_t le = cudaSuccess;
+  int c = from;
+  for (int i = 0; i < nsteps; ++i) {
+    cudaError_t r = launch_step(h, c);
+    if (r != cudaSuccess && le == cudaSuccess) le = r;
+    c = 1 - c;
+  }
+  e = cudaStreamEndCapture(h->stream, &g);
+  if (le != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return le;
+  }
+  if (e != cudaSuccess) return e;
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  return e;
+}
+
+// Staging area for host transfers: the population copy that does not hold the
+// current state (it is overwritten by the next step anyway).
+double* staging(rlbm_ctx* h) { return static_cast<double*>(h->pop[1 - h->cur]); }
+size_t staging_doubles(rlbm_ctx* h) { return h->L.pop_bytes / sizeof(double); }
+
+}  // namespace
+
+extern "C" {
+
+size_t rlbm_workspace_bytes(const rlbm_config* c) {
+  if (validate(c)) return 0;
+  Layout L;
+  make_layout(c, L);
+  return L.total;
+}
+
+int rlbm_create(const rlbm_config* c, rlbm_handle* out) {
+  if (!out) return RLBM_E_ARG;
+  *out = nullptr;
+  int v = validate(c);
+  if (v) return v;
+  rlbm_ctx* h = new (std::nothrow) rlbm_ctx();
+  if (!h) return RLBM_E_ARG;
+  h->edf = c->edf;
+  h->storage = c->storage;
+  h->ndom = c->ndomains;
+  h->doms.assign(c->domains, c->domains + c->ndomains);
+  make_layout(c, h->L);
+  if (!c->device_buffer || c->buffer_bytes < h->L.total ||
+      (reinterpret_cast<uintptr_t>(c->device_buffer) % kAlign)) {
+    delete h;
+    return RLBM_E_NOBUFFER;
+  }
+  for (const rlbm_domain& d : h->doms) h->cells += (long long)d.nx * d.ny;
+  h->base = static_cast<char*>(c->device_buffer);
+  h->d_status = reinterpret_cast<unsigned*>(h->base + h->L.status_off);
+  h->d_doms = reinterpret_cast<DomDev*>(h->base + h->L.doms_off);
+  h->d_tiles = reinterpret_cast<Tile*>(h->base + h->L.tiles_off);
+  h->pop[0] = h->base + h->L.pop_off[0];
+  h->pop[1] = h->base + h->L.pop_off[1];
+  h->initialized.assign(h->ndom, 0);
+  cudaError_t e = cudaSuccess;
+  if (c->cuda_stream) {
+    h->stream = static_cast<cudaStream_t>(c->cuda_stream);
+  } else {
+    e = cudaStreamCreate(&h->stream);  // blocking w.r.t. the legacy default stream
+    h->own_stream = true;
+  }
+  if (e == cudaSuccess) e = prepare_f64();
+  if (e == cudaSuccess) e = prepare_mixed();
+  if (e == cudaSuccess) e = cudaMallocHost(&h->h_status, sizeof(unsigned));
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->d_doms, h->L.dd.data(), sizeof(DomDev) * h->L.dd.size(),
+                        cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->d_tiles, h->L.tiles.data(), sizeof(Tile) * h->L.tiles.size(),
+                        cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = launch_prepare_refs(h->edf, h->d_doms, h->ndom, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    rlbm_destroy(h);
+    return RLBM_E_CUDA;
+  }
+  *out = h;
+  return RLBM_OK;
+}
+
+int rlbm_init(rlbm_handle h, int domain, int kind, const double* a, const double* theta,
+              const double* ux, const double* uy, int on_device) {
+  if (!h || domain < 0 || domain >= h->ndom || !a || !theta || !ux || !uy) return RLBM_E_ARG;
+  if (kind != RLBM_INIT_N_THETA && kind != RLBM_INIT_Z_THETA) return RLBM_E_ARG;
+  const rlbm_domain& d = h->doms[domain];
+  const size_t n = (size_t)d.nx * d.ny;
+  const double *da = a, *dt = theta, *dx = ux, *dy = uy;
+  cudaError_t e = cudaSuccess;
+  if (!on_device) {
+    if (4 * n > staging_doubles(h)) return RLBM_E_UNSUPPORTED;
+    double* s = staging(h);
+    e = cudaMemcpyAsync(s, a, n * 8, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s + n, theta, n * 8, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s + 2 * n, ux, n * 8, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s + 3 * n, uy, n * 8, cudaMemcpyHostToDevice, h->stream);
+    da = s; dt = s + n; dx = s + 2 * n; dy = s + 3 * n;
+  }
+  if (e != cudaSuccess) return RLBM_E_CUDA;
+  // status of this call only
+  unsigned saved = 0;
+  e = cudaMemcpyAsync(h->h_status, h->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return RLBM_E_CUDA;
+  saved = *h->h_status;
+  e = cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), h->stream);
+  InitArgs ia;
+  ia.doms = h->d_doms;
+  ia.dom = domain;
+  ia.kind = kind;
+  ia.a = da; ia.theta = dt; ia.ux = dx; ia.uy = dy;
+  ia.f = h->pop[h->cur];
+  ia.status = h->d_status;
+  if (e == cudaSuccess)
+    e = h->storage == RLBM_F64 ? launch_init_f64(h->edf, ia, d.nx, d.ny, h->stream)
+                               : launch_init_mixed(h->storage, h->edf, ia, d.nx, d.ny, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->h_status, h->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return RLBM_E_CUDA;
+  const unsigned st = *h->h_status;
+  // restore earlier step warnings so rlbm_sync_status still reports them
+  *h->h_status = saved;
+  e = cudaMemcpyAsync(h->d_status, h->h_status, sizeof(unsigned), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return RLBM_E_CUDA;
+  h->initialized[domain] = 1;
+  return (int)st;
+}
+
+int rlbm_step(rlbm_handle h, int nsteps) {
+  if (!h || nsteps < 0) return RLBM_E_ARG;
+  for (char v : h->initialized)
+    if (!v) return RLBM_E_STATE;
+  int launches = 0;
+  cudaError_t e = cudaSuccess;
+  int left = nsteps;
+  while (left >= 2 * kChunkPairs && e == cudaSuccess) {
+    if (!h->chunk_graph[h->cur]) e = capture(h, h->cur, 2 * kChunkPairs, &h->chunk_graph[h->cur]);
+    if (e == cudaSuccess) e = cudaGraphLaunch(h->chunk_graph[h->cur], h->stream);
+    left -= 2 * kChunkPairs;
+    launches += 2 * kChunkPairs;
+  }
+  while (left >= 2 && e == cudaSuccess) {
+    if (!h->pair_graph[h->cur]) e = capture(h, h->cur, 2, &h->pair_graph[h->cur]);
+    if (e == cudaSuccess) e = cudaGraphLaunch(h->pair_graph[h->cur], h->stream);
+    left -= 2;
+    launches += 2;
+  }
+  if (left == 1 && e == cudaSuccess) {
+    e = launch_step(h, h->cur);
+    h->cur = 1 - h->cur;
+    launches += 1;
+  }
+  h->last_updates = (long long)nsteps * h->cells;
+  h->last_launches = launches;
+  return cuda_fail(e);
+}
+
+int rlbm_moments(rlbm_handle h, int domain, int streamed, double* n, double* theta, double* ux,
+                 double* uy, double* z, int on_device) {
+  if (!h || domain < 0 || domain >= h->ndom || !n || !theta || !ux || !uy) return RLBM_E_ARG;
+  if (!h->initialized[domain]) return RLBM_E_STATE;
+  const rlbm_domain& d = h->doms[domain];
+  const size_t cnt = (size_t)d.nx * d.ny;
+  FieldsArgs fa;
+  fa.doms = h->d_doms;
+  fa.dom = domain;
+  fa.streamed = streamed ? 1 : 0;
+  fa.f = h->pop[h->cur];
+  fa.status = h->d_status;
+  if (on_device) {
+    fa.n = n; fa.theta = theta; fa.ux = ux; fa.uy = uy; fa.z = z;
+  } else {
+    if (5 * cnt > staging_doubles(h)) return RLBM_E_UNSUPPORTED;
+    double* s = staging(h);
+    fa.n = s; fa.theta = s + cnt; fa.ux = s + 2 * cnt; fa.uy = s + 3 * cnt; fa.z = s + 4 * cnt;
+  }
+  cudaError_t e = h->storage == RLBM_F64 ? launch_fields_f64(h->edf, fa, d.nx, d.ny, h->stream)
+                                          : launch_fields_mixed(h->storage, h->edf, fa, d.nx, d.ny, h->stream);
+  if (e == cudaSuccess && !on_device) {
+    double* outs[5] = {n, theta, ux, uy, z};
+    double* srcs[5] = {fa.n, fa.theta, fa.ux, fa.uy, fa.z};
+    for (int k = 0; k < 5 && e == cudaSuccess; ++k)
+      if (outs[k]) e = cudaMemcpyAsync(outs[k], srcs[k], cnt * 8, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  }
+  return cuda_fail(e);
+}
+
+static int copy_pops(rlbm_handle h, int domain, double* f, int on_device, int to_dense) {
+  if (!h || domain < 0 || domain >= h->ndom || !f) return RLBM_E_ARG;
+  const rlbm_domain& d = h->doms[domain];
+  const size_t per_plane = (size_t)(d.nx + 2) * (d.ny + 2);
+  CopyArgs ca;
+  ca.doms = h->d_doms;
+  ca.dom = domain;
+  ca.to_dense = to_dense;
+  ca.pop = h->pop[h->cur];
+  auto launch = [&](const CopyArgs& a) {
+    return h->storage == RLBM_F64 ? launch_copy_f64(a, h->stream) : launch_copy_mixed(h->storage, a, h->stream);
+  };
+  cudaError_t e = cudaSuccess;
+  if (on_device) {
+    ca.q0 = 0;
+    ca.nq = 72;
+    ca.dense = f;
+    e = launch(ca);
+  } else {
+    // stage through the spare population copy, as many planes at a time as fit
+    const int chunk = (int)std::min<size_t>(72, staging_doubles(h) / per_plane);
+    if (chunk < 1) return RLBM_E_UNSUPPORTED;
+    for (int q0 = 0; q0 < 72 && e == cudaSuccess; q0 += chunk) {
+      ca.q0 = q0;
+      ca.nq = std::min(chunk, 72 - q0);
+      ca.dense = staging(h);
+      const size_t bytes = (size_t)ca.nq * per_plane * sizeof(double);
+      double* host = f + (size_t)q0 * per_plane;
+      if (!to_dense) e = cudaMemcpyAsync(ca.dense, host, bytes, cudaMemcpyHostToDevice, h->stream);
+      if (e == cudaSuccess) e = launch(ca);
+      if (e == cudaSuccess && to_dense) e = cudaMemcpyAsync(host, ca.dense, bytes, cudaMemcpyDeviceToHost, h->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    }
+  }
+  if (e == cudaSuccess && !to_dense) h->initialized[domain] = 1;
+  return cuda_fail(e);
+}
+
+int rlbm_get_populations(rlbm_handle h, int domain, double* f, int on_device) {
+  if (h && domain >= 0 && domain < h->ndom && !h->initialized[domain]) return RLBM_E_STATE;
+  return copy_pops(h, domain, f, on_device, 1);
+}
+
+int rlbm_set_populations(rlbm_handle h, int domain, const double* f, int on_device) {
+  return copy_pops(h, domain, const_cast<double*>(f), on_device, 0);
+}
+
+int rlbm_tune(rlbm_handle h, int repeats) {
+  if (!h || repeats < 1) return RLBM_E_ARG;
+  for (char v : h->initialized)
+    if (!v) return RLBM_E_STATE;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return RLBM_E_CUDA;
+  const int ntiles = (int)h->L.tiles.size();
+  std::vector<int> cand = {ntiles};
+  for (int k : {1, 2, 3, 4, 6, 8})
+    if (k * sms < ntiles) cand.push_back(k * sms);
+  // keep the warnings accumulated so far; timing launches must not add any
+  e = cudaMemcpyAsync(h->h_status, h->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return RLBM_E_CUDA;
+  const unsigned saved = *h->h_status;
+  cudaEvent_t t0, t1;
+  if (cudaEventCreate(&t0) != cudaSuccess) return RLBM_E_CUDA;
+  if (cudaEventCreate(&t1) != cudaSuccess) { cudaEventDestroy(t0); return RLBM_E_CUDA; }
+  float best = 1e30f;
+  int best_grid = ntiles;
+  for (int g : cand) {
+    h->grid = g;
+    e = launch_step(h, h->cur);  // reads the current copy, writes the spare one
+    if (e == cudaSuccess) e = cudaEventRecord(t0, h->stream);
+    for (int r = 0; r < repeats && e == cudaSuccess; ++r) e = launch_step(h, h->cur);
+    if (e == cudaSuccess) e = cudaEventRecord(t1, h->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+    if (e != cudaSuccess) break;
+    if (ms < best) {
+      best = ms;
+      best_grid = g;
+    }
+  }
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  h->grid = best_grid;
+  for (int i = 0; i < 2; ++i) {
+    if (h->pair_graph[i]) cudaGraphExecDestroy(h->pair_graph[i]);
+    if (h->chunk_graph[i]) cudaGraphExecDestroy(h->chunk_graph[i]);
+    h->pair_graph[i] = h->chunk_graph[i] = nullptr;
+  }
+  *h->h_status = saved;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->d_status, h->h_status, sizeof(unsigned), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  return e == cudaSuccess ? best_grid : RLBM_E_CUDA;
+}
+
+int rlbm_sync_status(rlbm_handle h) {
+  if (!h) return RLBM_E_ARG;
+  cudaError_t e = cudaMemcpyAsync(h->h_status, h->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return RLBM_E_CUDA;
+  return (int)*h->h_status;
+}
+
+int rlbm_destroy(rlbm_handle h) {
+  if (!h) return RLBM_E_ARG;
+  for (int i = 0; i < 2; ++i) {
+    if (h->pair_graph[i]) cudaGraphExecDestroy(h->pair_graph[i]);
+    if (h->chunk_graph[i]) cudaGraphExecDestroy(h->chunk_graph[i]);
+  }
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  if (h->h_status) cudaFreeHost(h->h_status);
+  delete h;
+  return RLBM_OK;
+}
+
+const char* rlbm_status_string(int code) {
+  switch (code) {
+    case RLBM_OK: return "ok";
+    case RLBM_E_ARG: return "invalid argument";
+    case RLBM_E_CUDA: return "a CUDA call failed";
+    case RLBM_E_STATE: return "call out of order (initialise every domain first)";
+    case RLBM_E_UNSUPPORTED: return "unsupported combination";
+    case RLBM_E_NOBUFFER: return "device workspace missing, misaligned or too small";
+    default: break;
+  }
+  if (code > 0) {
+    if (code & RLBM_W_NONPHYSICAL) return "warning: non-physical state in some cell (left unrelaxed)";
+    if (code & RLBM_W_ZSOLVE) return "warning: fugacity solve did not converge in some cell";
+    if (code & RLBM_W_LANDAU_MAXITER) return "warning: Landau solve hit its iteration cap";
+    if (code & RLBM_W_CLAMPED_FUGACITY) return "warning: BE fugacity clamped to z_c";
+  }
+  return "unknown status";
+}
+
+int rlbm_last_step_info(rlbm_handle h, long long* cell_updates, int* kernel_launches) {
+  if (!h) return RLBM_E_ARG;
+  if (cell_updates) *cell_updates = h->last_updates;
+  if (kernel_launches) *kernel_launches = h->last_launches;
+  return RLBM_OK;
+}
+
+}  // extern "C"

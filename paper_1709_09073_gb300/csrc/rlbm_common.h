@@ -1,0 +1,55 @@
+// Definitions shared by the host side of the C ABI and the CUDA kernels.
+#pragma once
+#include <stddef.h>
+#include <stdint.h>
+
+namespace rlbm {
+
+enum { EDF_MJ = 0, EDF_FD = 1, EDF_BE = 2 };
+enum { BC_PERIODIC = 0, BC_ZERO_GRADIENT = 1, BC_WALL = 2 };
+enum { ST_F64 = 0, ST_F32 = 1, ST_BF16DEV = 2, ST_F16DEV = 3, ST_F32DEV = 4 };
+
+// per-cell status bits (identical to the public RLBM_W_* values)
+enum { ST_LANDAU = 1, ST_CLAMPED = 2, ST_NONPHYSICAL = 4, ST_ZSOLVE = 8 };
+
+constexpr double PI = 3.14159265358979323846264338327950288;
+constexpr double ZC = 1.0 - 1.0e-7;  // BE reference fugacity, Eq. (15)
+constexpr double SQRT3_2 = 0.86602540378443864676372317075294;
+
+// Halo-padded plane layout: element (x, y), x in [-1, nx], y in [-1, ny], of
+// population q lives at off + q * plane + (y + 1) * pitch + lpad + x, where
+// lpad = 16 bytes / element size (so x = 0 starts 16-byte aligned) and pitch
+// is a multiple of 128 bytes.
+struct DomDev {
+  int nx, ny, pitch, lpad;
+  long long plane;        // elements per population plane
+  long long off;          // element offset of plane 0 within a population copy
+  int bc[4];              // xlo, xhi, ylo, yhi
+  double inv_tau;
+  double t_wall[4];
+  double ref_n, ref_theta;  // reference rest equilibrium (deviation form of the mixed path)
+  double scale;             // deviation scale of the 16-bit storage
+  // filled on the device from (ref_n, ref_theta) at handle creation:
+  double zref[6];           // isotropic equilibrium moments Z_n0 of the reference state
+  double n0ref, t00ref;     // N^0 and T^00 of the FP32 reference populations fref
+  double zeff1, zeff2;      // n0ref, t00ref plus the N^0, T^00 of the residual rres
+  float fref[6];            // reference populations per shell (FP32)
+  float rres[6];            // FP64 reference equilibrium minus fref, per shell
+  float a_s[6];             // 16-bit storage: f = fref + a_s * h, a_s = fref * scale
+  float b_s[6];             // 1 / a_s
+};
+
+struct Tile {
+  int dom, x0, y0, pad;
+};
+
+struct StepArgs {
+  const DomDev* doms;
+  const Tile* tiles;
+  int ntiles;
+  const void* fin;        // population copy read (post-collision, with halo)
+  void* fout;             // population copy written
+  unsigned* status;       // OR of per-cell status bits
+};
+
+}  // namespace rlbm

@@ -1,0 +1,49 @@
+// Kernel launchers shared between the C ABI (rlbm_api.cu) and the kernel
+// translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "rlbm_common.h"
+
+namespace rlbm {
+
+struct InitArgs {
+  const DomDev* doms;
+  int dom, kind;
+  const double *a, *theta, *ux, *uy;  // device, [ny][nx]
+  void* f;                            // population copy to initialise
+  unsigned* status;
+};
+
+struct FieldsArgs {
+  const DomDev* doms;
+  int dom, streamed;
+  const void* f;
+  double *n, *theta, *ux, *uy, *z;    // device outputs, z may be null
+  unsigned* status;
+};
+
+struct CopyArgs {
+  const DomDev* doms;
+  int dom, to_dense;
+  int q0, nq;                         // planes q0 .. q0+nq-1
+  void* pop;
+  double* dense;                      // [nq][ny+2][nx+2]
+};
+
+// FP64 storage (plain method)
+cudaError_t prepare_f64();
+cudaError_t launch_step_f64(int edf, const StepArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_init_f64(int edf, const InitArgs& a, int nx, int ny, cudaStream_t s);
+cudaError_t launch_fields_f64(int edf, const FieldsArgs& a, int nx, int ny, cudaStream_t s);
+cudaError_t launch_copy_f64(const CopyArgs& a, cudaStream_t s);
+
+// FP32 / 16-bit deviation storage (mixed precision)
+cudaError_t prepare_mixed();
+cudaError_t launch_prepare_refs(int edf, DomDev* doms, int ndom, cudaStream_t s);
+cudaError_t launch_step_mixed(int storage, int edf, const StepArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_init_mixed(int storage, int edf, const InitArgs& a, int nx, int ny, cudaStream_t s);
+cudaError_t launch_fields_mixed(int storage, int edf, const FieldsArgs& a, int nx, int ny, cudaStream_t s);
+cudaError_t launch_copy_mixed(int storage, const CopyArgs& a, cudaStream_t s);
+
+}  // namespace rlbm

@@ -1,0 +1,615 @@
+// Mixed-precision step: FP32 / BF16 / FP16 storage, FP32 streaming, equilibrium
+// and relaxation carried out on deviations f - fref from each domain's rest
+// reference equilibrium, and FP64 for the quantities that set conservation:
+// the totals N^mu, T^{mu nu}, the Landau-frame solve (Eq. 21), n and eps, and the
+// degree-1 and degree-2 equilibrium moments.
+//
+// GB300 executes FP64 at 1/64 of the FP32 rate, so FP64 is confined to a few
+// dozen operations per cell: the 72-term moment sums run in FP32 on the small
+// deviations (their rounding error is relative to the deviation, not to f),
+// the Landau solve is FP32 Newton followed by two corrections with an FP64
+// residual, and the equilibrium moments that the collision must reproduce
+// exactly for N^0 and T^{mu 0} (Z_1k = n gamma (u_x + i u_y)^k P_1k,
+// Z_2k = eps gamma^2 (u_x + i u_y)^k P_2k) are formed from the FP64 n and eps.
+#include <cuda_runtime.h>
+
+#include "rlbm_kernels.cuh"
+
+namespace rlbm {
+
+// ------------------------------------------------------------- FP32 tables
+static __constant__ float c_pf[3][6] = {RLBM_PF_MJ_INIT, RLBM_PF_FD_INIT, RLBM_PF_BE_INIT};
+static __constant__ float c_Qf[3][126] = {RLBM_QF_MJ_INIT, RLBM_QF_FD_INIT, RLBM_QF_BE_INIT};
+// exact defects of the FP32 tables in the conserved moments (see eq_moments)
+static __constant__ double c_Ef[3][18] = {RLBM_EF_MJ_INIT, RLBM_EF_FD_INIT, RLBM_EF_BE_INIT};
+static __constant__ float c_p2f[3][6];
+static __constant__ float c_pnkf[63];
+constexpr int kSerF = 16, kExpBEf = 16, kExpFDf = 26;
+static __constant__ float c_invpowf[6 * kSerF];
+static __constant__ float c_be_expf[6 * kExpBEf];
+static __constant__ float c_fd_expf[6 * kExpFDf];
+static __constant__ float c_be_logcoeff[6];
+static __constant__ float c_be_harmf[6];
+static __constant__ float c_g_zcf[6];
+
+constexpr float kPIf = 3.14159265358979f;
+constexpr float kH = 0.866025403784438647f;
+constexpr float kRZCf = (float)RLBM_R_ZC;
+constexpr float kZCf = 0.9999999f;
+
+// --------------------------------------------------- FP32 EDF integrals g_nu
+__device__ __forceinline__ void li_series6f(float x, float g[6]) {
+  float xk = 1.0f;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) g[i] = 0.0f;
+#pragma unroll 4
+  for (int k = 1; k <= kSerF; ++k) {
+    xk *= x;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) g[i] = fmaf(xk, c_invpowf[i * kSerF + k - 1], g[i]);
+  }
+}
+
+template <int EDF>
+__device__ void g_allf(float z, float g[6]) {
+  if (EDF == EDF_MJ) {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) g[i] = z;
+    return;
+  }
+  if (EDF == EDF_BE) {
+    if (z <= 0.25f) { li_series6f(z, g); return; }
+    const float mu = logf(z);
+    float mk = 1.0f;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) g[i] = 0.0f;
+#pragma unroll 4
+    for (int k = 0; k < kExpBEf; ++k) {
+#pragma unroll
+      for (int i = 0; i < 6; ++i) g[i] = fmaf(mk, c_be_expf[i * kExpBEf + k], g[i]);
+      mk *= mu;
+    }
+    const float lnm = logf(-mu);
+    float mp = 1.0f;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      g[i] = fmaf(mp, c_be_harmf[i] - c_be_logcoeff[i] * lnm, g[i]);
+      mp *= mu;
+    }
+    return;
+  }
+  if (z <= 0.25f) {
+    li_series6f(-z, g);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) g[i] = -g[i];
+    return;
+  }
+  if (z <= 4.0f) {
+    const float mu = logf(z);
+    float mk = 1.0f;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) g[i] = 0.0f;
+#pragma unroll 2
+    for (int k = 0; k < kExpFDf; ++k) {
+#pragma unroll
+      for (int i = 0; i < 6; ++i) g[i] = fmaf(mk, c_fd_expf[i * kExpFDf + k], g[i]);
+      mk *= mu;
+    }
+    return;
+  }
+  li_series6f(-1.0f / z, g);
+  const float L = logf(z);
+  const float eta2 = 0.822467033f, eta4 = 0.947032829f, eta6 = 0.985551091f;
+  const float L2 = L * L, L3 = L2 * L, L4 = L3 * L, L5 = L4 * L, L6 = L5 * L;
+  g[0] = -g[0] + L;
+  g[1] = g[1] + L2 / 2.0f + 2.0f * eta2;
+  g[2] = -g[2] + L3 / 6.0f + 2.0f * eta2 * L;
+  g[3] = g[3] + L4 / 24.0f + eta2 * L2 + 2.0f * eta4;
+  g[4] = -g[4] + L5 / 120.0f + eta2 * L3 / 3.0f + 2.0f * eta4 * L;
+  g[5] = g[5] + L6 / 720.0f + eta2 * L4 / 12.0f + eta4 * L2 + 2.0f * eta6;
+}
+
+// Fugacity from g_3^2/g_2^3 = target (Eq. 25), FP32 safeguarded Newton in mu = ln z.
+template <int EDF>
+__device__ int solve_z_R_f(float target, float& z, float g[6]) {
+  if (EDF == EDF_BE && target < kRZCf) {
+    z = kZCf;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) g[i] = c_g_zcf[i];
+    return ST_CLAMPED;
+  }
+  float lo = -40.0f, hi = (EDF == EDF_BE) ? -1.0e-7f : 40.0f;
+  const float lt = logf(target);
+  float mu = fminf(fmaxf(-lt, lo + 1e-3f), hi);
+  int st = ST_ZSOLVE;
+  float dprev = INFINITY;
+  for (int it = 0; it < 40; ++it) {
+    g_allf<EDF>(expf(mu), g);
+    const float F = logf(g[2] * g[2] / (g[1] * g[1] * g[1])) - lt;
+    if (F == 0.0f) { st = 0; break; }
+    const float dF = 2.0f * g[1] / g[2] - 3.0f * g[0] / g[1];
+    if (F > 0.0f) lo = mu; else hi = mu;
+    float mn = mu - F / dF;
+    if (!(mn >= lo && mn <= hi)) mn = 0.5f * (lo + hi);
+    const float d = fabsf(mn - mu);
+    mu = mn;
+    if (d <= 4e-7f * fmaxf(1.0f, fabsf(mu)) || (d < 1e-4f && d >= dprev)) { st = 0; break; }
+    dprev = d;
+  }
+  z = expf(mu);
+  g_allf<EDF>(z, g);
+  return st;
+}
+
+// Fugacity from (n, theta): n = 2 pi theta^2 g_2(z), FP32.
+template <int EDF>
+__device__ int solve_z_nt_f(float n, float theta, float& z, float g[6]) {
+  const float G = n / (2.0f * kPIf * theta * theta);
+  if (EDF == EDF_MJ) {
+    z = G;
+    g_allf<EDF>(z, g);
+    return 0;
+  }
+  if (EDF == EDF_BE && G >= c_g_zcf[1]) {
+    z = kZCf;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) g[i] = c_g_zcf[i];
+    return ST_CLAMPED;
+  }
+  float lo = -40.0f, hi = (EDF == EDF_BE) ? -1.0e-7f : 40.0f;
+  const float lG = logf(G);
+  float mu = fminf(fmaxf(lG, lo + 1e-3f), hi);
+  int st = ST_ZSOLVE;
+  float dprev = INFINITY;
+  for (int it = 0; it < 40; ++it) {
+    g_allf<EDF>(expf(mu), g);
+    const float F = logf(g[1]) - lG;
+    if (F == 0.0f) { st = 0; break; }
+    const float dF = g[0] / g[1];
+    if (F < 0.0f) lo = mu; else hi = mu;
+    float mn = mu - F / dF;
+    if (!(mn >= lo && mn <= hi)) mn = 0.5f * (lo + hi);
+    const float d = fabsf(mn - mu);
+    mu = mn;
+    if (d <= 4e-7f * fmaxf(1.0f, fabsf(mu)) || (d < 1e-4f && d >= dprev)) { st = 0; break; }
+    dprev = d;
+  }
+  z = expf(mu);
+  g_allf<EDF>(z, g);
+  return st;
+}
+
+// ------------------------------------------------------------- Landau frame
+// T^a_b U^b = eps U^a (Eq. 21) as m - Pi u = (T00 - m.u) u. FP32 Newton from the
+// ideal-fluid estimate, then two Newton corrections whose residual is evaluated
+// in FP64 (the FP32 Jacobian only scales the correction), which brings u to
+// FP64 accuracy. gamma is refined from rsqrtf by one FP64 Newton step.
+__device__ __forceinline__ int landau_mixed(const double Td[6], double& ux, double& uy, double& eps,
+                                            double& gamma) {
+  const float E = (float)Td[0], mx = (float)Td[1], my = (float)Td[2], pxx = (float)Td[3],
+              pxy = (float)Td[4], pyy = (float)Td[5];
+  const float disc = 9.0f * E * E - 8.0f * (mx * mx + my * my);
+  if (!(E > 0.0f) || !(disc >= 0.0f)) return ST_NONPHYSICAL;
+  const float x = 0.25f * (3.0f * E + sqrtf(disc));
+  float fu = mx / x, fv = my / x;
+#pragma unroll
+  for (int it = 0; it < 3; ++it) {
+    const float a = E - (mx * fu + my * fv);
+    const float fx = mx - (pxx * fu + pxy * fv) - a * fu;
+    const float fy = my - (pxy * fu + pyy * fv) - a * fv;
+    const float j00 = fu * mx - pxx - a, j01 = fu * my - pxy, j10 = fv * mx - pxy, j11 = fv * my - pyy - a;
+    const float rdet = 1.0f / (j00 * j11 - j01 * j10);
+    fu += (j01 * fy - j11 * fx) * rdet;
+    fv += (j10 * fx - j00 * fy) * rdet;
+  }
+  double u = fu, v = fv;
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const double a = Td[0] - (Td[1] * u + Td[2] * v);
+    const double rx = Td[1] - (Td[3] * u + Td[4] * v) - a * u;
+    const double ry = Td[2] - (Td[4] * u + Td[5] * v) - a * v;
+    const float af = (float)a, uf = (float)u, vf = (float)v;
+    const float j00 = uf * mx - pxx - af, j01 = uf * my - pxy, j10 = vf * mx - pxy, j11 = vf * my - pyy - af;
+    const float rdet = 1.0f / (j00 * j11 - j01 * j10);
+    const float fx = (float)rx, fy = (float)ry;
+    u += (double)((j01 * fy - j11 * fx) * rdet);
+    v += (double)((j10 * fx - j00 * fy) * rdet);
+  }
+  const double w = 1.0 - (u * u + v * v);
+  if (!(w > 0.0)) return ST_NONPHYSICAL;
+  const float gf = rsqrtf((float)w);
+  const double g0 = gf;
+  gamma = g0 * (1.5 - 0.5 * w * g0 * g0);
+  ux = u;
+  uy = v;
+  eps = Td[0] - (Td[1] * u + Td[2] * v);
+  if (!(eps > 0.0) || !(fabsf(fu) < 1.0f)) return ST_NONPHYSICAL;
+  return 0;
+}
+
+// FP32 harmonic sums of a 12-vector (pairs d, d+6 folded first).
+struct HarmF {
+  float h0, c1, s1, c2, s2;
+};
+
+__device__ __forceinline__ HarmF harmonics_f(const float v[12]) {
+  float e[6], o[6];
+#pragma unroll
+  for (int d = 0; d < 6; ++d) {
+    e[d] = v[d] + v[d + 6];
+    o[d] = v[d] - v[d + 6];
+  }
+  HarmF H;
+  H.h0 = ((e[0] + e[1]) + (e[2] + e[3])) + (e[4] + e[5]);
+  H.c1 = fmaf(kH, o[1] - o[5], fmaf(0.5f, o[2] - o[4], o[0]));
+  H.s1 = fmaf(kH, o[2] + o[4], fmaf(0.5f, o[1] + o[5], o[3]));
+  H.c2 = fmaf(0.5f, (e[1] - e[2]) + (e[5] - e[4]), e[0] - e[3]);
+  H.s2 = kH * ((e[1] + e[2]) - (e[4] + e[5]));
+  return H;
+}
+
+// FP32 deviation of the equilibrium from fref for shell s (12 directions):
+// R^{c|s}_k = sum_n Qf^(k)_{s n} dZ_nk (+ rres_s in R^c_0), then the folded
+// 12-point synthesis (same symmetries as the FP64 form).
+template <int EDF>
+__device__ __forceinline__ void dfeq_shell(int s, float rres, const float zr[21], const float zi[21],
+                                           float fe[12]) {
+  float Rc[6], Rs[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    float ac = 0.0f, as = 0.0f;
+#pragma unroll
+    for (int n = k; n < 6; ++n) {
+      const float q = c_Qf[EDF][qoff(k) + s * (6 - k) + (n - k)];
+      ac = fmaf(q, zr[n * (n + 1) / 2 + k], ac);
+      as = fmaf(q, zi[n * (n + 1) / 2 + k], as);
+    }
+    Rc[k] = ac;
+    Rs[k] = as;
+  }
+  Rc[0] += rres;
+  const float t1 = Rc[0] + Rc[4], t2 = fmaf(-0.5f, Rc[4], Rc[0]), h2 = 0.5f * Rc[2];
+  const float Ec0 = t1 + Rc[2], Ec3 = t1 - Rc[2], Ec1 = t2 + h2, Ec2 = t2 - h2;
+  const float Es1 = kH * (Rs[2] + Rs[4]), Es2 = kH * (Rs[2] - Rs[4]);
+  const float E0 = Ec0, E1 = Ec1 + Es1, E2 = Ec2 + Es2, E3 = Ec3, E4 = Ec2 - Es2, E5 = Ec1 - Es1;
+  const float Oc0 = Rc[1] + Rc[3] + Rc[5], Oc1 = kH * (Rc[1] - Rc[5]), Oc2 = fmaf(0.5f, Rc[1] + Rc[5], -Rc[3]);
+  const float Os1 = fmaf(0.5f, Rs[1] + Rs[5], Rs[3]), Os2 = kH * (Rs[1] - Rs[5]), Os3 = Rs[1] - Rs[3] + Rs[5];
+  const float O0 = Oc0, O1 = Oc1 + Os1, O2 = Oc2 + Os2, O3 = Os3, O4 = Os2 - Oc2, O5 = Os1 - Oc1;
+  fe[0] = E0 + O0; fe[6] = E0 - O0;
+  fe[1] = E1 + O1; fe[7] = E1 - O1;
+  fe[2] = E2 + O2; fe[8] = E2 - O2;
+  fe[3] = E3 + O3; fe[9] = E3 - O3;
+  fe[4] = E4 + O4; fe[10] = E4 - O4;
+  fe[5] = E5 + O5; fe[11] = E5 - O5;
+}
+
+// FP32 equilibrium-moment deviations dZ_nk = Z_nk - Z_ref (Appendix, harmonic
+// form); Z_1k and Z_2k come from the FP64 n gamma and eps gamma^2 when given
+// (nG >= 0), otherwise everything is FP32 (wall ghosts).
+template <int EDF>
+__device__ __forceinline__ void dz_moments(const DomDev& D, const float g[6], float theta, float ux, float uy,
+                                           float gam, double nG, double eG2, double u2d, float zr[21],
+                                           float zi[21]) {
+  const float u2 = ux * ux + uy * uy;
+  float wr[6], wi[6];
+  wr[0] = 1.0f;
+  wi[0] = 0.0f;
+#pragma unroll
+  for (int k = 1; k < 6; ++k) {
+    wr[k] = wr[k - 1] * ux - wi[k - 1] * uy;
+    wi[k] = wr[k - 1] * uy + wi[k - 1] * ux;
+  }
+  float A = 2.0f * kPIf * theta;
+#pragma unroll
+  for (int n = 0; n < 6; ++n) {
+    if (n > 0) A *= (float)n * theta * gam;
+    float An = A * g[n];
+    if (nG >= 0.0 && n == 1) An = (float)nG;
+    if (nG >= 0.0 && n == 2) An = (float)eG2;
+#pragma unroll
+    for (int k = 0; k <= n; ++k) {
+      const int i = n * (n + 1) / 2 + k;
+      const float P = fmaf(u2, fmaf(u2, c_pnkf[3 * i + 2], c_pnkf[3 * i + 1]), c_pnkf[3 * i + 0]);
+      const float sc = An * P;
+      zr[i] = sc * wr[k];
+      zi[i] = sc * wi[k];
+    }
+    // isotropic part relative to the reference (n = 1, 2 set below)
+    const int i0 = n * (n + 1) / 2;
+    if (!(nG >= 0.0 && (n == 1 || n == 2))) zr[i0] -= (float)D.zref[n];
+  }
+  if (nG >= 0.0) {
+    // Conserved moments in FP64: the deviation equilibrium's N^0, T^00 (block 0)
+    // and T^0x, T^0y (block 1) must equal n gamma - N^0_ref, eps gamma^2 (1 + u^2/2)
+    // - T^00_ref and Z_21 exactly. The references include the residual rres; the
+    // FP32 tables' defects (c_Ef) are removed as in the FP64 path.
+    double dz10 = nG - D.zeff1;
+    double dz20 = eG2 * (1.0 + 0.5 * u2d) - D.zeff2;
+    double d10 = c_Ef[EDF][1] * dz10 + c_Ef[EDF][2] * dz20;
+    double d20 = c_Ef[EDF][7] * dz10 + c_Ef[EDF][8] * dz20;
+#pragma unroll
+    for (int n = 0; n < 6; ++n) {
+      if (n == 1 || n == 2) continue;
+      d10 = fma(c_Ef[EDF][n], (double)zr[n * (n + 1) / 2], d10);
+      d20 = fma(c_Ef[EDF][6 + n], (double)zr[n * (n + 1) / 2], d20);
+    }
+    double d21r = 0.0, d21i = 0.0;
+#pragma unroll
+    for (int n = 1; n < 6; ++n) {
+      d21r = fma(c_Ef[EDF][12 + n], (double)zr[n * (n + 1) / 2 + 1], d21r);
+      d21i = fma(c_Ef[EDF][12 + n], (double)zi[n * (n + 1) / 2 + 1], d21i);
+    }
+    zr[1] = (float)(dz10 - d10);
+    zr[3] = (float)(dz20 - d20);
+    zr[4] = (float)((double)zr[4] - d21r);
+    zi[4] = (float)((double)zi[4] - d21i);
+  }
+}
+
+// Halo writer of the mixed step: copies of the cell's deviation (smem column)
+// and, at fixed-T walls, the FP32 equilibrium deviation of the wall ghost.
+template <int EDF, class S>
+__device__ void write_halo_mixed(const DomDev& D, int x, int y, typename S::T* __restrict__ fout, const float* smf,
+                                 int tid, bool have_state, float n, float ux, float uy, float gam, unsigned& st) {
+  int hx[8], hy[8], wall[8];
+  const int cnt = halo_targets(D, x, y, hx, hy, wall);
+  const long long P = D.plane;
+  for (int i = 0; i < cnt; ++i) {
+    const long long h = (long long)(hy[i] + 1) * D.pitch + D.lpad + hx[i];
+    if (wall[i] < 0 || !have_state) {
+      for (int q = 0; q < 72; ++q) fout[q * P + h] = S::encf(smf[q * kThreads + tid], D, q % 6);
+    } else {
+      const float tw = (float)D.t_wall[wall[i]];
+      float z, g[6];
+      st |= solve_z_nt_f<EDF>(n, tw, z, g);
+      float zr[21], zi[21];
+      dz_moments<EDF>(D, g, tw, ux, uy, gam, -1.0, 0.0, 0.0, zr, zi);
+#pragma unroll 1
+      for (int s = 0; s < 6; ++s) {
+        float fe[12];
+        dfeq_shell<EDF>(s, D.rres[s], zr, zi, fe);
+        for (int d = 0; d < 12; ++d) fout[(6 * d + s) * P + h] = S::encf(fe[d], D, s);
+      }
+    }
+  }
+}
+
+template <int EDF, class S>
+__global__ void __launch_bounds__(kThreads) k_step_mixed(StepArgs a) {
+  extern __shared__ float smf[];
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+    const Tile tl = a.tiles[t];
+    const DomDev& D = a.doms[tl.dom];
+    const int x = tl.x0 + threadIdx.x, y = tl.y0 + threadIdx.y;
+    if (x >= D.nx || y >= D.ny) continue;
+    const long long P = D.plane;
+    const int W = D.pitch;
+    const typename S::T* __restrict__ fin = static_cast<const typename S::T*>(a.fin) + D.off;
+    typename S::T* __restrict__ fout = static_cast<typename S::T*>(a.fout) + D.off;
+    const long long c = (long long)(y + 1) * W + D.lpad + x;
+    // pull (FP32, deviation form) with the FP32 deviation moment sums
+    float A[12], B[12];
+#define RLBM_PULL_DIR(d)                                                        \
+  {                                                                             \
+    float a_ = 0.0f, b_ = 0.0f;                                                 \
+    _Pragma("unroll") for (int s = 0; s < 6; ++s) {                             \
+      const float v = S::decf(pull_one<d, float, S>(fin + (6 * d + s) * P, c, W), D, s); \
+      smf[(6 * d + s) * kThreads + tid] = v;                                    \
+      a_ = fmaf(v, c_pf[EDF][s], a_);                                           \
+      b_ = fmaf(v, c_p2f[EDF][s], b_);                                          \
+    }                                                                           \
+    A[d] = a_;                                                                  \
+    B[d] = b_;                                                                  \
+  }
+    RLBM_PULL_DIR(0) RLBM_PULL_DIR(1) RLBM_PULL_DIR(2) RLBM_PULL_DIR(3)
+    RLBM_PULL_DIR(4) RLBM_PULL_DIR(5) RLBM_PULL_DIR(6) RLBM_PULL_DIR(7)
+    RLBM_PULL_DIR(8) RLBM_PULL_DIR(9) RLBM_PULL_DIR(10) RLBM_PULL_DIR(11)
+#undef RLBM_PULL_DIR
+    const HarmF ha = harmonics_f(A), hb = harmonics_f(B);
+    // FP64 totals: reference moments + deviation sums
+    const double N0 = D.n0ref + (double)ha.h0;
+    const double H0 = D.t00ref + (double)hb.h0;
+    double Td[6];
+    Td[0] = H0;
+    Td[1] = hb.c1;
+    Td[2] = hb.s1;
+    Td[3] = 0.5 * (H0 + (double)hb.c2);
+    Td[4] = 0.5 * (double)hb.s2;
+    Td[5] = 0.5 * (H0 - (double)hb.c2);
+    double ux, uy, eps, gam;
+    unsigned st = landau_mixed(Td, ux, uy, eps, gam);
+    double n = 0.0;
+    if (!(st & ST_NONPHYSICAL)) {
+      n = gam * (N0 - (ux * (double)ha.c1 + uy * (double)ha.s1));
+      if (!(n > 0.0) || !isfinite(n)) st |= ST_NONPHYSICAL;
+    }
+    const bool ok = !(st & ST_NONPHYSICAL);
+    const float uxf = (float)ux, uyf = (float)uy, gf = (float)gam, nf = (float)n;
+    if (ok) {
+      const float ef = (float)eps;
+      float theta, z, g[6];
+      if (EDF == EDF_MJ) {
+        theta = ef / (2.0f * nf);
+        z = nf / (2.0f * kPIf * theta * theta);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) g[i] = z;
+      } else {
+        const float target = 0.5f * kPIf * ef * ef / (nf * nf * nf);
+        const int zs = solve_z_R_f<EDF>(target, z, g);
+        st |= zs;
+        if (zs & ST_CLAMPED) theta = sqrtf(nf / (2.0f * kPIf * g[1]));
+        else theta = 0.5f * g[1] / g[2] * ef / nf;
+      }
+      float zr[21], zi[21];
+      dz_moments<EDF>(D, g, theta, uxf, uyf, gf, n * gam, eps * gam * gam, ux * ux + uy * uy, zr, zi);
+      const float itau = (float)D.inv_tau;
+      float om[12];
+#pragma unroll
+      for (int d = 0; d < 12; ++d) om[d] = gf * (1.0f - ((float)dcos(d) * uxf + (float)dsin(d) * uyf)) * itau;
+#pragma unroll 1
+      for (int s = 0; s < 6; ++s) {
+        float fe[12];
+        dfeq_shell<EDF>(s, D.rres[s], zr, zi, fe);
+#pragma unroll
+        for (int d = 0; d < 12; ++d) {
+          const int q = 6 * d + s;
+          const float v = smf[q * kThreads + tid];
+          const float r = fmaf(om[d], fe[d] - v, v);
+          smf[q * kThreads + tid] = r;
+          fout[q * P + c] = S::encf(r, D, s);
+        }
+      }
+    } else {
+      for (int q = 0; q < 72; ++q) fout[q * P + c] = S::encf(smf[q * kThreads + tid], D, q % 6);
+    }
+    write_halo_mixed<EDF, S>(D, x, y, fout, smf, tid, ok, nf, uxf, uyf, gf, st);
+    if (st) atomicOr(a.status, st);
+  }
+}
+
+// Reference rest equilibrium of every domain (FP64), its FP32 rounding and
+// the reference moments, written into the device descriptors.
+template <int EDF>
+__global__ void k_prepare_refs(DomDev* doms, int ndom) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ndom) return;
+  DomDev& D = doms[i];
+  double z, g[6];
+  solve_z_from_n_theta<EDF>(D.ref_n, D.ref_theta, z, g);
+  double fact = 1.0, th = D.ref_theta, thp = th;
+  for (int n = 0; n < 6; ++n) {
+    if (n > 0) { fact *= n; thp *= th; }
+    D.zref[n] = 2.0 * PI * fact * g[n] * thp * c_pnk[3 * (n * (n + 1) / 2)];
+  }
+  double n0 = 0.0, t00 = 0.0;
+  for (int s = 0; s < 6; ++s) {
+    double fe = 0.0;
+    for (int n = 0; n < 6; ++n) fe += c_Q[EDF][qoff(0) + s * 6 + n] * D.zref[n];
+    const float ff = (float)fe;
+    D.fref[s] = ff;
+    D.rres[s] = (float)(fe - (double)ff);
+    const float as = (float)((double)ff * D.scale);
+    D.a_s[s] = as;
+    D.b_s[s] = 1.0f / as;
+    n0 += 12.0 * (double)ff * c_p[EDF][s];
+    t00 += 12.0 * (double)ff * c_p2[EDF][s];
+  }
+  D.n0ref = n0;
+  D.t00ref = t00;
+  double r1 = 0.0, r2 = 0.0;
+  for (int s = 0; s < 6; ++s) {
+    r1 += 12.0 * (double)D.rres[s] * (double)c_pf[EDF][s];
+    r2 += 12.0 * (double)D.rres[s] * (double)c_p2f[EDF][s];
+  }
+  D.zeff1 = n0 + r1;
+  D.zeff2 = t00 + r2;
+}
+
+// ------------------------------------------------------------- launchers
+static const double h_p2[3][6] = {RLBM_P2_MJ_INIT, RLBM_P2_FD_INIT, RLBM_P2_BE_INIT};
+static const double h_pnk[63] = RLBM_PNK_INIT;
+static const double h_invpow[6 * RLBM_NSERIES] = RLBM_INVPOW_INIT;
+static const double h_be_exp[6 * RLBM_NEXP] = RLBM_BE_EXP_INIT;
+static const double h_fd_exp[6 * RLBM_NEXP] = RLBM_FD_EXP_INIT;
+static const double h_be_logcoef[6] = RLBM_BE_LOGCOEF_INIT;
+static const double h_be_harm[6] = RLBM_BE_HARM_INIT;
+static const double h_g_zc[6] = RLBM_G_ZC_INIT;
+
+constexpr size_t kSmemF = 72 * kThreads * sizeof(float);
+
+template <class S>
+static cudaError_t prepare_s() {
+  cudaError_t e;
+  if ((e = prepare_common_t<S, EDF_MJ>())) return e;
+  if ((e = prepare_common_t<S, EDF_FD>())) return e;
+  return prepare_common_t<S, EDF_BE>();
+}
+
+// Upload the FP32 tables (converted once from the FP64 tables) and opt the FP64
+// helper kernels into 72 KB of shared memory.
+cudaError_t prepare_mixed() {
+  float p2f[3][6], pnk[63], inv[6 * kSerF], be[6 * kExpBEf], fd[6 * kExpFDf], lc[6], hm[6], gz[6];
+  for (int e = 0; e < 3; ++e)
+    for (int s = 0; s < 6; ++s) p2f[e][s] = (float)h_p2[e][s];
+  for (int i = 0; i < 63; ++i) pnk[i] = (float)h_pnk[i];
+  for (int nu = 0; nu < 6; ++nu) {
+    for (int k = 0; k < kSerF; ++k) inv[nu * kSerF + k] = (float)h_invpow[nu * RLBM_NSERIES + k];
+    for (int k = 0; k < kExpBEf; ++k) be[nu * kExpBEf + k] = (float)h_be_exp[nu * RLBM_NEXP + k];
+    for (int k = 0; k < kExpFDf; ++k) fd[nu * kExpFDf + k] = (float)h_fd_exp[nu * RLBM_NEXP + k];
+    lc[nu] = (float)h_be_logcoef[nu];
+    hm[nu] = (float)h_be_harm[nu];
+    gz[nu] = (float)h_g_zc[nu];
+  }
+  cudaError_t e;
+  if ((e = cudaMemcpyToSymbol(c_p2f, p2f, sizeof(p2f)))) return e;
+  if ((e = cudaMemcpyToSymbol(c_pnkf, pnk, sizeof(pnk)))) return e;
+  if ((e = cudaMemcpyToSymbol(c_invpowf, inv, sizeof(inv)))) return e;
+  if ((e = cudaMemcpyToSymbol(c_be_expf, be, sizeof(be)))) return e;
+  if ((e = cudaMemcpyToSymbol(c_fd_expf, fd, sizeof(fd)))) return e;
+  if ((e = cudaMemcpyToSymbol(c_be_logcoeff, lc, sizeof(lc)))) return e;
+  if ((e = cudaMemcpyToSymbol(c_be_harmf, hm, sizeof(hm)))) return e;
+  if ((e = cudaMemcpyToSymbol(c_g_zcf, gz, sizeof(gz)))) return e;
+  if ((e = prepare_s<StoreF32>())) return e;
+  if ((e = prepare_s<StoreBF16>())) return e;
+  if ((e = prepare_s<StoreF32Dev>())) return e;
+  return prepare_s<StoreF16>();
+}
+
+cudaError_t launch_prepare_refs(int edf, DomDev* doms, int ndom, cudaStream_t s) {
+  const int grid = (ndom + 63) / 64;
+  switch (edf) {
+    case EDF_MJ: k_prepare_refs<EDF_MJ><<<grid, 64, 0, s>>>(doms, ndom); break;
+    case EDF_FD: k_prepare_refs<EDF_FD><<<grid, 64, 0, s>>>(doms, ndom); break;
+    default: k_prepare_refs<EDF_BE><<<grid, 64, 0, s>>>(doms, ndom); break;
+  }
+  return cudaGetLastError();
+}
+
+template <class S>
+static cudaError_t step_s(int edf, const StepArgs& a, int grid, cudaStream_t s) {
+  switch (edf) {
+    case EDF_MJ: k_step_mixed<EDF_MJ, S><<<grid, dim3(32, 4), kSmemF, s>>>(a); break;
+    case EDF_FD: k_step_mixed<EDF_FD, S><<<grid, dim3(32, 4), kSmemF, s>>>(a); break;
+    default: k_step_mixed<EDF_BE, S><<<grid, dim3(32, 4), kSmemF, s>>>(a); break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step_mixed(int storage, int edf, const StepArgs& a, int grid, cudaStream_t s) {
+  switch (storage) {
+    case ST_F32: return step_s<StoreF32>(edf, a, grid, s);
+    case ST_F32DEV: return step_s<StoreF32Dev>(edf, a, grid, s);
+    case ST_BF16DEV: return step_s<StoreBF16>(edf, a, grid, s);
+    default: return step_s<StoreF16>(edf, a, grid, s);
+  }
+}
+
+cudaError_t launch_init_mixed(int storage, int edf, const InitArgs& a, int nx, int ny, cudaStream_t s) {
+  switch (storage) {
+    case ST_F32: return launch_init_t<StoreF32>(edf, a, nx, ny, s);
+    case ST_F32DEV: return launch_init_t<StoreF32Dev>(edf, a, nx, ny, s);
+    case ST_BF16DEV: return launch_init_t<StoreBF16>(edf, a, nx, ny, s);
+    default: return launch_init_t<StoreF16>(edf, a, nx, ny, s);
+  }
+}
+
+cudaError_t launch_fields_mixed(int storage, int edf, const FieldsArgs& a, int nx, int ny, cudaStream_t s) {
+  switch (storage) {
+    case ST_F32: return launch_fields_t<StoreF32>(edf, a, nx, ny, s);
+    case ST_F32DEV: return launch_fields_t<StoreF32Dev>(edf, a, nx, ny, s);
+    case ST_BF16DEV: return launch_fields_t<StoreBF16>(edf, a, nx, ny, s);
+    default: return launch_fields_t<StoreF16>(edf, a, nx, ny, s);
+  }
+}
+
+cudaError_t launch_copy_mixed(int storage, const CopyArgs& a, cudaStream_t s) {
+  switch (storage) {
+    case ST_F32: return launch_copy_t<StoreF32>(a, s);
+    case ST_F32DEV: return launch_copy_t<StoreF32Dev>(a, s);
+    case ST_BF16DEV: return launch_copy_t<StoreBF16>(a, s);
+    default: return launch_copy_t<StoreF16>(a, s);
+  }
+}
+
+}  // namespace rlbm

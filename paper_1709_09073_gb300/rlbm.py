@@ -1,0 +1,210 @@
+"""Python binding of the C ABI in include/rlbm.h (argument marshalling only).
+
+Every step of the method runs in the CUDA library librlbm.so. PyTorch provides
+device memory (the workspace) and the CUDA stream. There is no fallback: if
+the library cannot be loaded, every call raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import workloads as W
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "librlbm.so")
+
+RLBM_MJ, RLBM_FD, RLBM_BE = 0, 1, 2
+RLBM_F64, RLBM_F32, RLBM_BF16DEV, RLBM_F16DEV, RLBM_F32DEV = 0, 1, 2, 3, 4
+RLBM_PERIODIC, RLBM_ZERO_GRADIENT, RLBM_FIXED_T_WALL = 0, 1, 2
+RLBM_INIT_N_THETA, RLBM_INIT_Z_THETA = 0, 1
+RLBM_OK = 0
+RLBM_W_LANDAU_MAXITER, RLBM_W_CLAMPED_FUGACITY, RLBM_W_NONPHYSICAL, RLBM_W_ZSOLVE = 1, 2, 4, 8
+RLBM_E_ARG, RLBM_E_CUDA, RLBM_E_STATE, RLBM_E_UNSUPPORTED, RLBM_E_NOBUFFER = -1, -2, -3, -4, -5
+
+EXPORTS = ["rlbm_workspace_bytes", "rlbm_create", "rlbm_init", "rlbm_step", "rlbm_moments",
+           "rlbm_get_populations", "rlbm_set_populations", "rlbm_tune", "rlbm_sync_status",
+           "rlbm_destroy", "rlbm_status_string", "rlbm_last_step_info"]
+
+
+class rlbm_domain(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("tau", ctypes.c_double),
+                ("bc_xlo", ctypes.c_int), ("bc_xhi", ctypes.c_int),
+                ("bc_ylo", ctypes.c_int), ("bc_yhi", ctypes.c_int),
+                ("t_wall_xlo", ctypes.c_double), ("t_wall_xhi", ctypes.c_double),
+                ("t_wall_ylo", ctypes.c_double), ("t_wall_yhi", ctypes.c_double),
+                ("ref_n", ctypes.c_double), ("ref_theta", ctypes.c_double),
+                ("scale", ctypes.c_double)]
+
+
+class rlbm_config(ctypes.Structure):
+    _fields_ = [("ndomains", ctypes.c_int), ("domains", ctypes.POINTER(rlbm_domain)),
+                ("edf", ctypes.c_int), ("storage", ctypes.c_int), ("order", ctypes.c_int),
+                ("device_buffer", ctypes.c_void_p), ("buffer_bytes", ctypes.c_size_t),
+                ("cuda_stream", ctypes.c_void_p)]
+
+
+_lib = None
+_D = ctypes.POINTER(ctypes.c_double)
+_H = ctypes.c_void_p
+
+
+def load(path=None):
+    """Load librlbm.so (built in-tree by paper_1709_09073_gb300.build). Raises if missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError("librlbm.so not found at %s: build it with "
+                           "`python -m paper_1709_09073_gb300.build` (no CPU fallback exists)" % p)
+    L = ctypes.CDLL(p)
+    L.rlbm_workspace_bytes.argtypes = [ctypes.POINTER(rlbm_config)]
+    L.rlbm_workspace_bytes.restype = ctypes.c_size_t
+    L.rlbm_create.argtypes = [ctypes.POINTER(rlbm_config), ctypes.POINTER(_H)]
+    L.rlbm_init.argtypes = [_H, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+    L.rlbm_step.argtypes = [_H, ctypes.c_int]
+    L.rlbm_moments.argtypes = [_H, ctypes.c_int, ctypes.c_int] + [ctypes.c_void_p] * 5 + [ctypes.c_int]
+    L.rlbm_get_populations.argtypes = [_H, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]
+    L.rlbm_set_populations.argtypes = [_H, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]
+    L.rlbm_tune.argtypes = [_H, ctypes.c_int]
+    L.rlbm_sync_status.argtypes = [_H]
+    L.rlbm_destroy.argtypes = [_H]
+    L.rlbm_status_string.argtypes = [ctypes.c_int]
+    L.rlbm_status_string.restype = ctypes.c_char_p
+    L.rlbm_last_step_info.argtypes = [_H, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_int)]
+    _lib = L
+    return L
+
+
+class RlbmError(RuntimeError):
+    pass
+
+
+def _check(code):
+    if code < 0:
+        raise RlbmError("rlbm error %d: %s" % (code, load().rlbm_status_string(code).decode()))
+    return code
+
+
+def make_domains(specs):
+    arr = (rlbm_domain * len(specs))()
+    for i, d in enumerate(specs):
+        arr[i] = rlbm_domain(d.nx, d.ny, d.tau, *d.bc, *d.t_wall, d.ref_n, d.ref_theta, d.scale)
+    return arr
+
+
+def rlbm_workspace_bytes(specs, edf, storage, order=5):
+    doms = make_domains(specs)
+    cfg = rlbm_config(len(specs), doms, edf, storage, order, None, 0, None)
+    return load().rlbm_workspace_bytes(ctypes.byref(cfg))
+
+
+def _ptr(x):
+    """Device pointer of a torch tensor, or host pointer of a numpy array."""
+    if hasattr(x, "data_ptr"):
+        return ctypes.c_void_p(x.data_ptr()), 1
+    return x.ctypes.data_as(ctypes.c_void_p), 0
+
+
+class Simulation:
+    """One handle over a torch-allocated workspace; all compute in librlbm."""
+
+    def __init__(self, specs, edf=RLBM_MJ, storage=RLBM_F64, device="cuda", stream=None, order=5):
+        import torch
+        self.torch = torch
+        self.specs = list(specs)
+        self.edf, self.storage = edf, storage
+        L = load()
+        self._doms = make_domains(self.specs)
+        cfg = rlbm_config(len(self.specs), self._doms, edf, storage, order, None, 0, None)
+        nbytes = L.rlbm_workspace_bytes(ctypes.byref(cfg))
+        if nbytes == 0:
+            raise RlbmError("invalid configuration")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.workspace.device)
+        cfg.device_buffer = ctypes.c_void_p(self.workspace.data_ptr())
+        cfg.buffer_bytes = nbytes
+        cfg.cuda_stream = ctypes.c_void_p(self.stream.cuda_stream)
+        self.h = _H()
+        _check(L.rlbm_create(ctypes.byref(cfg), ctypes.byref(self.h)))
+
+    def init(self, domain, state):
+        """Initialise from a workloads.InitialState (host numpy or device torch fields)."""
+        fields = [state.a, state.theta, state.ux, state.uy]
+        if hasattr(state.a, "data_ptr"):
+            ptrs = [ctypes.c_void_p(f.contiguous().data_ptr()) for f in fields]
+            on_dev = 1
+        else:
+            fields = [np.ascontiguousarray(f, dtype=np.float64) for f in fields]
+            ptrs = [f.ctypes.data_as(ctypes.c_void_p) for f in fields]
+            on_dev = 0
+        return _check(load().rlbm_init(self.h, domain, state.kind, *ptrs, on_dev))
+
+    def step(self, nsteps):
+        return _check(load().rlbm_step(self.h, nsteps))
+
+    def moments(self, domain, streamed=True, on_device=False):
+        """Return (n, theta, ux, uy, z) as numpy arrays (or torch tensors on device)."""
+        if not 0 <= domain < len(self.specs):
+            dummy = np.empty(1)
+            p = dummy.ctypes.data_as(ctypes.c_void_p)
+            _check(load().rlbm_moments(self.h, domain, 1, p, p, p, p, p, 0))
+        d = self.specs[domain]
+        if on_device:
+            outs = [self.torch.empty((d.ny, d.nx), dtype=self.torch.float64, device=self.workspace.device)
+                    for _ in range(5)]
+            ptrs = [ctypes.c_void_p(o.data_ptr()) for o in outs]
+        else:
+            outs = [np.empty((d.ny, d.nx)) for _ in range(5)]
+            ptrs = [o.ctypes.data_as(ctypes.c_void_p) for o in outs]
+        _check(load().rlbm_moments(self.h, domain, 1 if streamed else 0, *ptrs, 1 if on_device else 0))
+        return outs
+
+    def get_populations(self, domain):
+        d = self.specs[domain]
+        f = np.empty((72, d.ny + 2, d.nx + 2))
+        _check(load().rlbm_get_populations(self.h, domain, f.ctypes.data_as(ctypes.c_void_p), 0))
+        return f
+
+    def set_populations(self, domain, f):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        _check(load().rlbm_set_populations(self.h, domain, f.ctypes.data_as(ctypes.c_void_p), 0))
+
+    def tune(self, repeats=3):
+        """Autotune the step launch (grid shape) on the current state; returns the grid."""
+        return _check(load().rlbm_tune(self.h, repeats))
+
+    def sync_status(self):
+        return _check(load().rlbm_sync_status(self.h))
+
+    def last_step_info(self):
+        u, k = ctypes.c_longlong(), ctypes.c_int()
+        _check(load().rlbm_last_step_info(self.h, ctypes.byref(u), ctypes.byref(k)))
+        return u.value, k.value
+
+    def close(self):
+        if self.h:
+            load().rlbm_destroy(self.h)
+            self.h = _H()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def status_string(code):
+    return load().rlbm_status_string(code).decode()
+
+
+def from_workload(wl, storage=RLBM_F64, **kw):
+    """Create a Simulation for a workloads.Workload and initialise every domain."""
+    edf = wl.domains[0].edf
+    sim = Simulation(wl.domains, edf=edf, storage=storage, **kw)
+    st = 0
+    for i, s in enumerate(wl.init):
+        st |= sim.init(i, s)
+    return sim, st

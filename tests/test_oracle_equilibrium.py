@@ -43,8 +43,10 @@ def _trig_coeffs(n, q):
     return a, b
 
 
-def _I2_from_oracle(orc, edf, m, n, q, th, ux, uy, z):
-    M = orc.eq_moments(edf, th, ux, uy, z)
+def _I2_from_oracle(orc, edf, m, n, q, th, ux, uy, z, quad=True):
+    """I_2^{mnq} rebuilt from the oracle's harmonic moments: by default those of the
+    direct angular quadrature, which uses nothing of the closed forms."""
+    M = orc.eq_moments_quad(edf, th, ux, uy, z) if quad else orc.eq_moments(edf, th, ux, uy, z)
     bn, bk, bc = orc.basis()
     idx = {(int(bn[i]), int(bk[i]), int(bc[i])): i for i in range(36)}
     d = m + n + q
@@ -79,6 +81,18 @@ def test_polylog_against_mpmath(orc, nu):
 
 
 @pytest.mark.parametrize("edf,th,ux,uy,z", CASES)
+def test_closed_form_moments_equal_quadrature(orc, edf, th, ux, uy, z):
+    """The oracle's harmonic moments from the Appendix closed forms equal those of
+    the direct angular quadrature of their definition."""
+    a = orc.eq_moments(edf, th, ux, uy, z)
+    b = orc.eq_moments_quad(edf, th, ux, uy, z)
+    bn, _, _ = orc.basis()
+    for i in range(36):
+        scale = abs(b[[j for j in range(36) if bn[j] == bn[i]][0]])
+        assert abs(a[i] - b[i]) <= 2e-14 * scale, (i, a[i], b[i])
+
+
+@pytest.mark.parametrize("edf,th,ux,uy,z", CASES)
 def test_moments_match_appendix_closed_forms(orc, edf, th, ux, uy, z):
     """All 56 printed I_2^{mnq} against the oracle's angular-quadrature moments."""
     for (m, n, q), expr in _appendix().items():
@@ -105,7 +119,7 @@ def test_moments_brute_force_2d_integral(orc, edf, mnq):
         return integrate.quad(fn, 0, np.inf, epsabs=0, epsrel=1e-13, limit=200)[0]
 
     ref = integrate.quad(inner, 0, 2 * math.pi, epsabs=0, epsrel=1e-12, limit=200)[0]
-    got = _I2_from_oracle(orc, edf, m, n, q, th, ux, uy, z)
+    got = _I2_from_oracle(orc, edf, m, n, q, th, ux, uy, z, quad=False)
     scale = _I2_from_oracle(orc, edf, m + n + q, 0, 0, th, ux, uy, z)
     assert abs(got - ref) <= 1e-9 * abs(scale)
 
