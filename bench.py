@@ -31,8 +31,8 @@ from paper_1709_09073_gb300 import workloads as W  # noqa: E402
 
 METRIC = "lattice updates/s (MLUPS) FP64 vs mixed+batched on 1 GB300; % roofline"
 UNIT = "MLUPS"
-BYTES_PER_CELL = {0: 1152, 1: 576, 2: 288, 3: 288}   # 2 x 72 x element size
-STORAGE_NAME = {0: "f64", 1: "f32", 2: "bf16dev", 3: "f16dev"}
+BYTES_PER_CELL = {0: 1152, 1: 576, 2: 288, 3: 288, 4: 576}   # 2 x 72 x element size
+STORAGE_NAME = {0: "f64", 1: "f32", 2: "bf16dev", 3: "f16dev", 4: "f32dev"}
 
 
 def dist_env():
@@ -164,7 +164,7 @@ def run_native(args):
     rlbm.load()
     wl = W.batched_taylor_green(seed=20260101 + rank)
     cells = wl.cells
-    storage = rlbm.RLBM_F32
+    storage = rlbm.RLBM_F32DEV
     sim, st0 = rlbm.from_workload(wl, storage=storage)
     grid = sim.tune(3)
     sim.step(args.warmup)
@@ -182,11 +182,11 @@ def run_native(args):
     bpc = BYTES_PER_CELL[storage]
     achieved = bpc * cells / per_launch / 1e9
     hbm_peak, peak_kind = peaks()
-    tr = traffic_record("k_step_mixed_f32_mj")
+    tr = traffic_record("k_step_mixed_f32dev_mj")
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(achieved / hbm_peak, 4),
                 "traffic": round(tr * cells) if tr else None,
-                "peak_source": peak_kind, "kernel": "k_step_mixed<MJ, F32>",
+                "peak_source": peak_kind, "kernel": "k_step_mixed<MJ, F32Dev>",
                 "algorithmic_bytes_per_cell": bpc}
     launches = sim.last_step_info()[1]
 
@@ -256,11 +256,12 @@ def run_native(args):
         line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": round(t / args.steps * 1e3, 4), "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 totals and Landau solve)",
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 totals, Landau solve, n, eps)",
                 "data": "synthetic",
                 "config": {"workload": wl.name, "domains": len(wl.domains), "cells_per_gpu": cells,
                            "sides": "uniform 32..512 (seed 20260101 + rank)", "tau": "0.55..2.0",
-                           "u0": "0.005..0.05", "edf": "MJ", "order": 5, "storage": "f32",
+                           "u0": "0.005..0.05", "edf": "MJ", "order": 5,
+                           "storage": "f32dev (FP32 populations as relative deviations from the rest equilibrium)",
                            "grid": grid, "l2": "inputs larger than L2 (%.1f GB of populations)"
                            % (2 * 288 * cells / 1e9), "parallelism": "independent domains per GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
@@ -296,6 +297,22 @@ def cpu_baseline(wl, budget_s=15.0):
     return {"value": round(done_cells / t_used / 1e6, 4), "unit": UNIT, "cores": O.num_threads(),
             "kind": "oracle",
             "sample": "1 step of each of the first %d domains (%d cells) of the workload" % (ndom, done_cells)}
+
+
+def run_profile_case(args):
+    """A small case for ncu: one domain, init and a few steps of one kernel.
+    mixed: 2048 x 2048 Taylor-Green, MJ, FP32 deviations (2.4 GB of populations);
+    fp64:  1024 x 1024 Taylor-Green, MJ, FP64 (1.2 GB). Inputs exceed L2."""
+    import torch
+    from paper_1709_09073_gb300 import build, rlbm
+    build.build()
+    rlbm.load()
+    L, storage = (2048, rlbm.RLBM_F32DEV) if args.profile_case == "mixed" else (1024, rlbm.RLBM_F64)
+    wl = W.taylor_green(L=L, u0=0.02, tau=0.9, steps=3)
+    sim, _ = rlbm.from_workload(wl, storage=storage)
+    sim.step(3)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": args.profile_case, "cells": wl.cells, "status": sim.sync_status()}))
 
 
 def run_reference(args):
@@ -352,10 +369,14 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--profile-case", choices=["mixed", "fp64"], default=None,
+                    help="run a small single-domain case for ncu instead of the benchmark")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.impl == "reference":
+    if args.profile_case:
+        run_profile_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_native(args)

@@ -71,8 +71,10 @@ void orc_lattice(int edf, double p[6], double w[6], double cphi[12], double sphi
 
 /* ------------------------------------------------------------- polylogarithms */
 
-/* Bernoulli numbers B_{2j}, j = 0..15 (B_0 = 1), as exact rationals. */
+/* Bernoulli numbers B_{2j}, j = 0..15 (B_0 = 1), as exact rationals. The
+ * expansions below never ask beyond B_30 (NAN if they did). */
 static double bernoulli_even(int j) {
+  if (j < 0 || j > 15) return NAN;
   static const double num[16] = {1.0, 1.0, -1.0, 1.0, -1.0, 5.0, -691.0, 7.0, -3617.0, 43867.0,
                                  -174611.0, 854513.0, -236364091.0, 8553103.0, -23749461029.0,
                                  8615841276005.0};
@@ -123,8 +125,8 @@ double orc_g(int edf, int nu, double z) {
     if (!(z < 1.0) || z < 0.0) return NAN;
     if (z <= 0.5) return li_series(nu, z);
     double mu = log(z);
-    double sum = 0.0, term = 1.0; /* term = mu^k / k! */
-    for (int k = 0; k <= 40; ++k) {
+    double sum = 0.0, term = 1.0; /* term = mu^k / k!; |mu| < ln 2 so 30 terms suffice */
+    for (int k = 0; k <= 30; ++k) {
       if (k > 0) term *= mu / k;
       if (k == nu - 1) {
         double H = 0.0;
