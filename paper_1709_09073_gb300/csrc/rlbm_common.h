@@ -33,6 +33,8 @@ struct DomDev {
   double zref[6];           // isotropic equilibrium moments Z_n0 of the reference state
   double n0ref, t00ref;     // N^0 and T^00 of the FP32 reference populations fref
   double zeff1, zeff2;      // n0ref, t00ref plus the N^0, T^00 of the residual rres
+  float n0_hl[2], t00_hl[2], z1_hl[2], z2_hl[2];  // the same four as double-float pairs
+  float zref_f[6];          // zref rounded to FP32
   float fref[6];            // reference populations per shell (FP32)
   float rres[6];            // FP64 reference equilibrium minus fref, per shell
   float a_s[6];             // 16-bit storage: f = fref + a_s * h, a_s = fref * scale

@@ -13,6 +13,7 @@
 // Z_2k = eps gamma^2 (u_x + i u_y)^k P_2k) are formed from the FP64 n and eps.
 #include <cuda_runtime.h>
 
+#include "rlbm_dfloat.cuh"
 #include "rlbm_kernels.cuh"
 
 namespace rlbm {
@@ -21,7 +22,7 @@ namespace rlbm {
 static __constant__ float c_pf[3][6] = {RLBM_PF_MJ_INIT, RLBM_PF_FD_INIT, RLBM_PF_BE_INIT};
 static __constant__ float c_Qf[3][126] = {RLBM_QF_MJ_INIT, RLBM_QF_FD_INIT, RLBM_QF_BE_INIT};
 // exact defects of the FP32 tables in the conserved moments (see eq_moments)
-static __constant__ double c_Ef[3][18] = {RLBM_EF_MJ_INIT, RLBM_EF_FD_INIT, RLBM_EF_BE_INIT};
+static __constant__ float c_Ef[3][18] = {RLBM_EF_MJ_INIT, RLBM_EF_FD_INIT, RLBM_EF_BE_INIT};
 static __constant__ float c_p2f[3][6];
 static __constant__ float c_pnkf[63];
 constexpr int kSerF = 16, kExpBEf = 16, kExpFDf = 26;
@@ -181,13 +182,12 @@ __device__ int solve_z_nt_f(float n, float theta, float& z, float g[6]) {
 
 // ------------------------------------------------------------- Landau frame
 // T^a_b U^b = eps U^a (Eq. 21) as m - Pi u = (T00 - m.u) u. FP32 Newton from the
-// ideal-fluid estimate, then two Newton corrections whose residual is evaluated
-// in FP64 (the FP32 Jacobian only scales the correction), which brings u to
-// FP64 accuracy. gamma is refined from rsqrtf by one FP64 Newton step.
-__device__ __forceinline__ int landau_mixed(const double Td[6], double& ux, double& uy, double& eps,
-                                            double& gamma) {
-  const float E = (float)Td[0], mx = (float)Td[1], my = (float)Td[2], pxx = (float)Td[3],
-              pxy = (float)Td[4], pyy = (float)Td[5];
+// ideal-fluid estimate, then one Newton correction whose residual is evaluated
+// in double-float (the FP32 Jacobian only scales the small correction), which
+// brings u to ~1e-15. eps, gamma follow in double-float. T = {T00, T01, T02,
+// T11, T12, T22}.
+__device__ __forceinline__ int landau_df(const df T[6], df& ux, df& uy, df& eps, df& gamma) {
+  const float E = T[0].hi, mx = T[1].hi, my = T[2].hi, pxx = T[3].hi, pxy = T[4].hi, pyy = T[5].hi;
   const float disc = 9.0f * E * E - 8.0f * (mx * mx + my * my);
   if (!(E > 0.0f) || !(disc >= 0.0f)) return ST_NONPHYSICAL;
   const float x = 0.25f * (3.0f * E + sqrtf(disc));
@@ -202,28 +202,22 @@ __device__ __forceinline__ int landau_mixed(const double Td[6], double& ux, doub
     fu += (j01 * fy - j11 * fx) * rdet;
     fv += (j10 * fx - j00 * fy) * rdet;
   }
-  double u = fu, v = fv;
-#pragma unroll
-  for (int c = 0; c < 2; ++c) {
-    const double a = Td[0] - (Td[1] * u + Td[2] * v);
-    const double rx = Td[1] - (Td[3] * u + Td[4] * v) - a * u;
-    const double ry = Td[2] - (Td[4] * u + Td[5] * v) - a * v;
-    const float af = (float)a, uf = (float)u, vf = (float)v;
-    const float j00 = uf * mx - pxx - af, j01 = uf * my - pxy, j10 = vf * mx - pxy, j11 = vf * my - pyy - af;
+  if (!(fu * fu + fv * fv < 1.0f)) return ST_NONPHYSICAL;
+  {
+    const df a = df_sub(T[0], df_add(df_mul(T[1], fu), df_mul(T[2], fv)));
+    const df rx = df_sub(df_sub(T[1], df_add(df_mul(T[3], fu), df_mul(T[4], fv))), df_mul(a, fu));
+    const df ry = df_sub(df_sub(T[2], df_add(df_mul(T[4], fu), df_mul(T[5], fv))), df_mul(a, fv));
+    const float af = a.hi;
+    const float j00 = fu * mx - pxx - af, j01 = fu * my - pxy, j10 = fv * mx - pxy, j11 = fv * my - pyy - af;
     const float rdet = 1.0f / (j00 * j11 - j01 * j10);
-    const float fx = (float)rx, fy = (float)ry;
-    u += (double)((j01 * fy - j11 * fx) * rdet);
-    v += (double)((j10 * fx - j00 * fy) * rdet);
+    const float gx = df_to_float(rx), gy = df_to_float(ry);
+    ux = two_sum(fu, (j01 * gy - j11 * gx) * rdet);
+    uy = two_sum(fv, (j10 * gx - j00 * gy) * rdet);
   }
-  const double w = 1.0 - (u * u + v * v);
-  if (!(w > 0.0)) return ST_NONPHYSICAL;
-  const float gf = rsqrtf((float)w);
-  const double g0 = gf;
-  gamma = g0 * (1.5 - 0.5 * w * g0 * g0);
-  ux = u;
-  uy = v;
-  eps = Td[0] - (Td[1] * u + Td[2] * v);
-  if (!(eps > 0.0) || !(fabsf(fu) < 1.0f)) return ST_NONPHYSICAL;
+  eps = df_sub(T[0], df_add(df_mul(T[1], ux), df_mul(T[2], uy)));
+  const df w = df_sub(df_make(1.0f, 0.0f), df_add(df_mul(ux, ux), df_mul(uy, uy)));
+  if (!(w.hi > 0.0f) || !(eps.hi > 0.0f)) return ST_NONPHYSICAL;
+  gamma = df_rsqrt(w);
   return 0;
 }
 
@@ -284,12 +278,12 @@ __device__ __forceinline__ void dfeq_shell(int s, float rres, const float zr[21]
 }
 
 // FP32 equilibrium-moment deviations dZ_nk = Z_nk - Z_ref (Appendix, harmonic
-// form); Z_1k and Z_2k come from the FP64 n gamma and eps gamma^2 when given
-// (nG >= 0), otherwise everything is FP32 (wall ghosts).
+// form). When An1, An2 >= 0 they replace the degree-1 and degree-2 prefactors
+// (n gamma and eps gamma^2 from the double-float state); the caller then sets
+// the conserved isotropic entries dZ_10, dZ_20 itself.
 template <int EDF>
 __device__ __forceinline__ void dz_moments(const DomDev& D, const float g[6], float theta, float ux, float uy,
-                                           float gam, double nG, double eG2, double u2d, float zr[21],
-                                           float zi[21]) {
+                                           float gam, float An1, float An2, float zr[21], float zi[21]) {
   const float u2 = ux * ux + uy * uy;
   float wr[6], wi[6];
   wr[0] = 1.0f;
@@ -304,8 +298,8 @@ __device__ __forceinline__ void dz_moments(const DomDev& D, const float g[6], fl
   for (int n = 0; n < 6; ++n) {
     if (n > 0) A *= (float)n * theta * gam;
     float An = A * g[n];
-    if (nG >= 0.0 && n == 1) An = (float)nG;
-    if (nG >= 0.0 && n == 2) An = (float)eG2;
+    if (n == 1 && An1 >= 0.0f) An = An1;
+    if (n == 2 && An2 >= 0.0f) An = An2;
 #pragma unroll
     for (int k = 0; k <= n; ++k) {
       const int i = n * (n + 1) / 2 + k;
@@ -314,35 +308,7 @@ __device__ __forceinline__ void dz_moments(const DomDev& D, const float g[6], fl
       zr[i] = sc * wr[k];
       zi[i] = sc * wi[k];
     }
-    // isotropic part relative to the reference (n = 1, 2 set below)
-    const int i0 = n * (n + 1) / 2;
-    if (!(nG >= 0.0 && (n == 1 || n == 2))) zr[i0] -= (float)D.zref[n];
-  }
-  if (nG >= 0.0) {
-    // Conserved moments in FP64: the deviation equilibrium's N^0, T^00 (block 0)
-    // and T^0x, T^0y (block 1) must equal n gamma - N^0_ref, eps gamma^2 (1 + u^2/2)
-    // - T^00_ref and Z_21 exactly. The references include the residual rres; the
-    // FP32 tables' defects (c_Ef) are removed as in the FP64 path.
-    double dz10 = nG - D.zeff1;
-    double dz20 = eG2 * (1.0 + 0.5 * u2d) - D.zeff2;
-    double d10 = c_Ef[EDF][1] * dz10 + c_Ef[EDF][2] * dz20;
-    double d20 = c_Ef[EDF][7] * dz10 + c_Ef[EDF][8] * dz20;
-#pragma unroll
-    for (int n = 0; n < 6; ++n) {
-      if (n == 1 || n == 2) continue;
-      d10 = fma(c_Ef[EDF][n], (double)zr[n * (n + 1) / 2], d10);
-      d20 = fma(c_Ef[EDF][6 + n], (double)zr[n * (n + 1) / 2], d20);
-    }
-    double d21r = 0.0, d21i = 0.0;
-#pragma unroll
-    for (int n = 1; n < 6; ++n) {
-      d21r = fma(c_Ef[EDF][12 + n], (double)zr[n * (n + 1) / 2 + 1], d21r);
-      d21i = fma(c_Ef[EDF][12 + n], (double)zi[n * (n + 1) / 2 + 1], d21i);
-    }
-    zr[1] = (float)(dz10 - d10);
-    zr[3] = (float)(dz20 - d20);
-    zr[4] = (float)((double)zr[4] - d21r);
-    zi[4] = (float)((double)zi[4] - d21i);
+    zr[n * (n + 1) / 2] -= D.zref_f[n];
   }
 }
 
@@ -363,7 +329,7 @@ __device__ void write_halo_mixed(const DomDev& D, int x, int y, typename S::T* _
       float z, g[6];
       st |= solve_z_nt_f<EDF>(n, tw, z, g);
       float zr[21], zi[21];
-      dz_moments<EDF>(D, g, tw, ux, uy, gam, -1.0, 0.0, 0.0, zr, zi);
+      dz_moments<EDF>(D, g, tw, ux, uy, gam, -1.0f, -1.0f, zr, zi);
 #pragma unroll 1
       for (int s = 0; s < 6; ++s) {
         float fe[12];
@@ -407,27 +373,27 @@ __global__ void __launch_bounds__(kThreads) k_step_mixed(StepArgs a) {
     RLBM_PULL_DIR(8) RLBM_PULL_DIR(9) RLBM_PULL_DIR(10) RLBM_PULL_DIR(11)
 #undef RLBM_PULL_DIR
     const HarmF ha = harmonics_f(A), hb = harmonics_f(B);
-    // FP64 totals: reference moments + deviation sums
-    const double N0 = D.n0ref + (double)ha.h0;
-    const double H0 = D.t00ref + (double)hb.h0;
-    double Td[6];
-    Td[0] = H0;
-    Td[1] = hb.c1;
-    Td[2] = hb.s1;
-    Td[3] = 0.5 * (H0 + (double)hb.c2);
-    Td[4] = 0.5 * (double)hb.s2;
-    Td[5] = 0.5 * (H0 - (double)hb.c2);
-    double ux, uy, eps, gam;
-    unsigned st = landau_mixed(Td, ux, uy, eps, gam);
-    double n = 0.0;
+    // moment totals in double-float: reference moments + FP32 deviation sums
+    const df N0 = df_add(df_make(D.n0_hl[0], D.n0_hl[1]), ha.h0);
+    const df H0 = df_add(df_make(D.t00_hl[0], D.t00_hl[1]), hb.h0);
+    df T[6];
+    T[0] = H0;
+    T[1] = df_make(hb.c1, 0.0f);
+    T[2] = df_make(hb.s1, 0.0f);
+    T[3] = df_scale(df_add(H0, hb.c2), 0.5f);
+    T[4] = df_make(0.5f * hb.s2, 0.0f);
+    T[5] = df_scale(df_add(H0, -hb.c2), 0.5f);
+    df ux, uy, eps, gam;
+    unsigned st = landau_df(T, ux, uy, eps, gam);
+    df n = df_make(0.0f, 0.0f);
     if (!(st & ST_NONPHYSICAL)) {
-      n = gam * (N0 - (ux * (double)ha.c1 + uy * (double)ha.s1));
-      if (!(n > 0.0) || !isfinite(n)) st |= ST_NONPHYSICAL;
+      n = df_mul(gam, df_sub(N0, df_add(df_mul(ux, ha.c1), df_mul(uy, ha.s1))));
+      if (!(n.hi > 0.0f) || !isfinite(n.hi)) st |= ST_NONPHYSICAL;
     }
     const bool ok = !(st & ST_NONPHYSICAL);
-    const float uxf = (float)ux, uyf = (float)uy, gf = (float)gam, nf = (float)n;
+    const float uxf = df_to_float(ux), uyf = df_to_float(uy), gf = df_to_float(gam), nf = df_to_float(n);
     if (ok) {
-      const float ef = (float)eps;
+      const float ef = df_to_float(eps);
       float theta, z, g[6];
       if (EDF == EDF_MJ) {
         theta = ef / (2.0f * nf);
@@ -441,8 +407,37 @@ __global__ void __launch_bounds__(kThreads) k_step_mixed(StepArgs a) {
         if (zs & ST_CLAMPED) theta = sqrtf(nf / (2.0f * kPIf * g[1]));
         else theta = 0.5f * g[1] / g[2] * ef / nf;
       }
+      // conserved equilibrium moments from the double-float state: Z_1k from
+      // n gamma, Z_2k from eps gamma^2 (a clamped BE state relaxes to its own
+      // equilibrium energy 4 pi theta^3 g_3(z_c))
+      const df nG = df_mul(n, gam);
+      df eG2 = df_mul(df_mul(eps, gam), gam);
+      if (st & ST_CLAMPED) eG2 = df_make(4.0f * kPIf * theta * theta * theta * g[2] * gf * gf, 0.0f);
       float zr[21], zi[21];
-      dz_moments<EDF>(D, g, theta, uxf, uyf, gf, n * gam, eps * gam * gam, ux * ux + uy * uy, zr, zi);
+      dz_moments<EDF>(D, g, theta, uxf, uyf, gf, nG.hi, eG2.hi, zr, zi);
+      // Z_20 = eps gamma^2 (1 + u^2/2), all in double-float
+      const df u2h = df_scale(df_add(df_mul(ux, ux), df_mul(uy, uy)), 0.5f);
+      const df dz10 = df_sub(nG, df_make(D.z1_hl[0], D.z1_hl[1]));
+      const df dz20 = df_sub(df_add(eG2, df_mul(eG2, u2h)), df_make(D.z2_hl[0], D.z2_hl[1]));
+      zr[1] = df_to_float(dz10);
+      zr[3] = df_to_float(dz20);
+      // remove the FP32 tables' defects in N^0, T^00, T^0x, T^0y (FP32 suffices:
+      // the corrections are ~1e-8 of the moments)
+      float d10 = 0.0f, d20 = 0.0f, d21r = 0.0f, d21i = 0.0f;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        d10 = fmaf(c_Ef[EDF][k], zr[k * (k + 1) / 2], d10);
+        d20 = fmaf(c_Ef[EDF][6 + k], zr[k * (k + 1) / 2], d20);
+      }
+#pragma unroll
+      for (int k = 1; k < 6; ++k) {
+        d21r = fmaf(c_Ef[EDF][12 + k], zr[k * (k + 1) / 2 + 1], d21r);
+        d21i = fmaf(c_Ef[EDF][12 + k], zi[k * (k + 1) / 2 + 1], d21i);
+      }
+      zr[1] -= d10;
+      zr[3] -= d20;
+      zr[4] -= d21r;
+      zi[4] -= d21i;
       const float itau = (float)D.inv_tau;
       float om[12];
 #pragma unroll
@@ -504,6 +499,13 @@ __global__ void k_prepare_refs(DomDev* doms, int ndom) {
   }
   D.zeff1 = n0 + r1;
   D.zeff2 = t00 + r2;
+  const double v4[4] = {D.n0ref, D.t00ref, D.zeff1, D.zeff2};
+  float* pairs[4] = {D.n0_hl, D.t00_hl, D.z1_hl, D.z2_hl};
+  for (int k = 0; k < 4; ++k) {
+    pairs[k][0] = (float)v4[k];
+    pairs[k][1] = (float)(v4[k] - (double)pairs[k][0]);
+  }
+  for (int n = 0; n < 6; ++n) D.zref_f[n] = (float)D.zref[n];
 }
 
 // ------------------------------------------------------------- launchers
