@@ -8,7 +8,8 @@ the host cores.
 
 Workload (headline): 256 periodic Taylor-Green domains of uneven size (sides
 uniform in 32..512, seed 20260101), MJ fifth-order equilibrium, tau swept
-0.55..2.0, amplitudes 0.005..0.05 c, FP32 populations, one launch per step over
+0.55..2.0, amplitudes 0.005..0.05 c, FP32 populations stored as deviations
+from each domain's rest equilibrium, one launch per step over
 a tile work list, autotuned grid, steps replayed from a CUDA graph. Under
 torchrun each rank runs its own independently seeded batch (weak scaling, no
 data-path collective); rank 0 prints one JSON line.
@@ -125,13 +126,25 @@ def timed_steps(sim, steps, torch):
     return e0.elapsed_time(e1) / 1e3
 
 
-def barrier_max(t, world, torch):
+def rank_workload(rank):
+    """The batch one rank advances: its own independently seeded set of domains
+    (the domains are independent problems, so ranks share no data; per-rank work
+    is fixed as the rank count grows: weak scaling)."""
+    return W.batched_taylor_green(seed=20260101 + rank)
+
+
+def over_ranks(x, world, torch, op="max", device="cuda"):
+    """Max (timings) or sum (cells) of a scalar over all ranks; metadata only."""
     if world == 1:
-        return t
+        return x
     import torch.distributed as dist
-    v = torch.tensor([t], dtype=torch.float64, device="cuda")
-    dist.all_reduce(v, op=dist.ReduceOp.MAX)
+    v = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(v, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
     return float(v.item())
+
+
+def barrier_max(t, world, torch):
+    return over_ranks(t, world, torch, "max")
 
 
 def barrier(world):
@@ -162,8 +175,9 @@ def run_native(args):
         dist.init_process_group("nccl")
     build.build()
     rlbm.load()
-    wl = W.batched_taylor_green(seed=20260101 + rank)
+    wl = rank_workload(rank)
     cells = wl.cells
+    total_cells = over_ranks(cells, world, torch, "sum")  # units all ranks process per step
     storage = rlbm.RLBM_F32DEV
     sim, st0 = rlbm.from_workload(wl, storage=storage)
     grid = sim.tune(3)
@@ -177,7 +191,7 @@ def run_native(args):
     barrier(world)
     t = barrier_max(t, world, torch)
     status = sim.sync_status()
-    value = cells * world * args.steps / t / 1e6
+    value = total_cells * args.steps / t / 1e6
     per_launch = t / args.steps
     bpc = BYTES_PER_CELL[storage]
     achieved = bpc * cells / per_launch / 1e9
@@ -218,7 +232,7 @@ def run_native(args):
     te = barrier_max(te, world, torch)
     h2d = 4 * 8 * cells
     d2h = 5 * 8 * cells + 4 * e2e_steps
-    e2e = {"value": round(cells * world * e2e_steps / te / 1e6, 2), "unit": UNIT,
+    e2e = {"value": round(total_cells * e2e_steps / te / 1e6, 2), "unit": UNIT,
            "h2d_bytes_per_step": int(h2d / e2e_steps), "d2h_bytes_per_step": int(d2h / e2e_steps),
            "steps": e2e_steps, "what": "upload fields -> rlbm_init -> (rlbm_step(1) + status read) x K -> "
                                        "rlbm_moments to pinned host"}
@@ -234,7 +248,7 @@ def run_native(args):
         k64 = max(2, args.steps // 20)
         barrier(world)
         t64 = barrier_max(timed_steps(sim64, k64, torch), world, torch)
-        v64 = cells * world * k64 / t64 / 1e6
+        v64 = total_cells * k64 / t64 / 1e6
         flops_per_cell = FP64_FLOPS_PER_CELL
         clk = (clocks or {}).get("sm_mhz") or 2070.0
         alu_peak = 152 * FP64_FLOP_PER_CLK_SM * clk * 1e6 / 1e12
@@ -259,6 +273,7 @@ def run_native(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 totals, Landau solve, n, eps)",
                 "data": "synthetic",
                 "config": {"workload": wl.name, "domains": len(wl.domains), "cells_per_gpu": cells,
+                           "cells_all_ranks": int(total_cells),
                            "sides": "uniform 32..512 (seed 20260101 + rank)", "tau": "0.55..2.0",
                            "u0": "0.005..0.05", "edf": "MJ", "order": 5,
                            "storage": "f32dev (FP32 populations as relative deviations from the rest equilibrium)",
@@ -272,10 +287,11 @@ def run_native(args):
         dist.destroy_process_group()
 
 
-# FP64 operations per cell update of the plain kernel (k_step_f64<MJ>), FMA = 2,
-# counted from the instruction mix that ncu reports for one launch (see
-# profiles/); used for the FP64 ALU roofline of the plain form.
-FP64_FLOPS_PER_CELL = 2900
+# FP64 operations per cell update of the plain kernel (k_step_f64<MJ>), FMA = 2:
+# 830 DFMA + 308 DADD + 202 DMUL per cell, the executed-instruction counts ncu
+# reports for one 1024^2 launch divided by its cells; used for the FP64 ALU
+# roofline of the plain form.
+FP64_FLOPS_PER_CELL = 2 * 830 + 308 + 202
 
 
 def cpu_baseline(wl, budget_s=15.0):
@@ -312,7 +328,9 @@ def run_profile_case(args):
     sim, _ = rlbm.from_workload(wl, storage=storage)
     sim.step(3)
     torch.cuda.synchronize()
-    print(json.dumps({"profile_case": args.profile_case, "cells": wl.cells, "status": sim.sync_status()}))
+    t = timed_steps(sim, args.steps, torch) if args.steps > 0 else 0.0
+    print(json.dumps({"profile_case": args.profile_case, "cells": wl.cells, "status": sim.sync_status(),
+                      "steps": args.steps, "mlups": round(wl.cells * args.steps / t / 1e6, 1) if t else None}))
 
 
 def run_reference(args):

@@ -31,16 +31,19 @@ def _sources_mtime():
     return max(os.path.getmtime(p) for p in paths)
 
 
-def build(force=False, verbose=False):
-    """Compile (if stale) and return the path of librlbm.so."""
-    os.makedirs(BUILD, exist_ok=True)
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _sources_mtime():
-        return LIB
+def build(force=False, verbose=False, defines=(), build_dir=None):
+    """Compile (if stale) and return the path of librlbm.so. `defines` adds -D
+    options (tuning variants); `build_dir` places the result elsewhere."""
+    bdir = build_dir or BUILD
+    lib = os.path.join(bdir, "librlbm.so")
+    os.makedirs(bdir, exist_ok=True)
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= _sources_mtime():
+        return lib
     exe = nvcc()
 
     def compile_unit(u):
-        obj = os.path.join(BUILD, u.replace(".cu", ".o"))
-        cmd = [exe] + ARCH + FLAGS + ["-c", os.path.join(CSRC, u), "-o", obj]
+        obj = os.path.join(bdir, u.replace(".cu", ".o"))
+        cmd = [exe] + ARCH + FLAGS + ["-D" + d for d in defines] + ["-c", os.path.join(CSRC, u), "-o", obj]
         if verbose:
             cmd += ["-Xptxas", "-v"]
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -53,13 +56,13 @@ def build(force=False, verbose=False):
     if verbose:
         for _, log in results:
             print(log)
-    tmp = LIB + ".%d.tmp" % os.getpid()
+    tmp = lib + ".%d.tmp" % os.getpid()
     cmd = [exe] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in results] + ["-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s" % r.stderr)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
