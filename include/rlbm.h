@@ -19,7 +19,8 @@
  *    on the host or on the device as the `on_device` argument says.
  *  - Device memory: the caller allocates ONE workspace of
  *    rlbm_workspace_bytes(config) bytes (256-byte aligned) and keeps it alive
- *    until rlbm_destroy; the library allocates no device memory of its own.
+ *    until rlbm_destroy; the library allocates no device memory of its own
+ *    (rlbm_step_noalloc, at the end, uses a fixed static array instead).
  *    The handle (host memory) and a captured CUDA graph belong to the library.
  *  - Streams: every call is ordered on config->cuda_stream (a cudaStream_t;
  *    NULL = the legacy default stream). rlbm_step is asynchronous; calls that
@@ -160,6 +161,50 @@ const char *rlbm_status_string(int code);
 /* Cells x steps executed by the last rlbm_step call and kernel launches it
  * issued (for throughput accounting). */
 int rlbm_last_step_info(rlbm_handle h, long long *cell_updates, int *kernel_launches);
+
+/* ---- Fixed-scratch step (no allocation) ----------------------------------
+ * The paper has no counterpart to this entry point: it is a service of the
+ * library for callers that cannot call cudaMalloc -- a host application whose
+ * own allocator has reserved the device memory and hands out nothing more, or
+ * code on a latency-critical path where cudaMalloc/cudaFree are banned because
+ * they can synchronise the whole device.
+ *
+ * Advances ONE domain by nsteps >= 0 steps of the plain method (FP64 storage
+ * and arithmetic, fifth order; the same step kernel as rlbm_step with
+ * RLBM_F64) without a handle or workspace and without allocating anything:
+ * no cudaMalloc, cudaFree or allocating library routine is called.
+ *  - domain: host descriptor, checked as rlbm_create checks it (ref_n,
+ *    ref_theta, scale ignored); edf: rlbm_edf.
+ *  - f_in, f_out: caller-owned DEVICE buffers, FP64 [72][ny+2][nx+2] with the
+ *    halo ring -- the layout of rlbm_get_populations -- holding the stored
+ *    post-collision populations before and after the steps. The halo of f_in
+ *    must be the one a step left (e.g. a checkpoint taken with
+ *    rlbm_get_populations(..., on_device = 1) or a previous f_out). f_out may
+ *    equal f_in. Neither is retained after the call.
+ *  - cuda_stream: cudaStream_t the work is ordered on (NULL = legacy default
+ *    stream). The call is asynchronous unless `warnings` is non-NULL: then it
+ *    waits for the stream and stores this call's warning bits (RLBM_W_*) there.
+ *  - Scratch: all working memory (two halo-padded copies, descriptor, tile
+ *    list, status word) lives in one file-scope device array of
+ *    RLBM_NOALLOC_SCRATCH_BYTES (32 MiB), which the CUDA runtime reserves on
+ *    every GPU where the library's module is loaded and holds until the
+ *    process exits. A domain fits when 1.5 KB + 16 * ceil(nx/32) * ceil(ny/4)
+ *    + 2 * 576 * (ny + 2) * pitch <= 32 MiB, pitch = nx + 3 rounded up to a
+ *    multiple of 16 (about 160 x 160 cells); a larger one returns
+ *    RLBM_E_SCRATCH before any device work.
+ *  - First call on each device: it looks up the array's device address
+ *    (cudaGetSymbolAddress) and sets the step kernel's shared-memory limit.
+ *    Make that first call before any stream capture begins.
+ *  - Sharing: every call on a device uses the same array, which keeps the last
+ *    call's contents (the status word is cleared at the start of each call).
+ *    Calls whose work overlaps on the GPU -- different streams, or host threads
+ *    that do not order their calls -- race on it and give undefined results.
+ * Returns RLBM_OK, RLBM_E_ARG, RLBM_E_SCRATCH, RLBM_E_UNSUPPORTED (device
+ * ordinal >= 64) or RLBM_E_CUDA. */
+#define RLBM_E_SCRATCH (-6)               /* domain too large for the fixed scratch */
+#define RLBM_NOALLOC_SCRATCH_BYTES (32u << 20)
+int rlbm_step_noalloc(const rlbm_domain *domain, int edf, int nsteps, const double *f_in,
+                      double *f_out, void *cuda_stream, unsigned *warnings);
 
 #ifdef __cplusplus
 }

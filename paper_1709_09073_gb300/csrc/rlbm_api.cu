@@ -480,6 +480,7 @@ const char* rlbm_status_string(int code) {
     case RLBM_E_STATE: return "call out of order (initialise every domain first)";
     case RLBM_E_UNSUPPORTED: return "unsupported combination";
     case RLBM_E_NOBUFFER: return "device workspace missing, misaligned or too small";
+    case RLBM_E_SCRATCH: return "domain too large for the fixed scratch of rlbm_step_noalloc";
     default: break;
   }
   if (code > 0) {

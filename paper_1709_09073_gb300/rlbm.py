@@ -21,10 +21,12 @@ RLBM_INIT_N_THETA, RLBM_INIT_Z_THETA = 0, 1
 RLBM_OK = 0
 RLBM_W_LANDAU_MAXITER, RLBM_W_CLAMPED_FUGACITY, RLBM_W_NONPHYSICAL, RLBM_W_ZSOLVE = 1, 2, 4, 8
 RLBM_E_ARG, RLBM_E_CUDA, RLBM_E_STATE, RLBM_E_UNSUPPORTED, RLBM_E_NOBUFFER = -1, -2, -3, -4, -5
+RLBM_E_SCRATCH = -6
+RLBM_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 EXPORTS = ["rlbm_workspace_bytes", "rlbm_create", "rlbm_init", "rlbm_step", "rlbm_moments",
            "rlbm_get_populations", "rlbm_set_populations", "rlbm_tune", "rlbm_sync_status",
-           "rlbm_destroy", "rlbm_status_string", "rlbm_last_step_info"]
+           "rlbm_destroy", "rlbm_status_string", "rlbm_last_step_info", "rlbm_step_noalloc"]
 
 
 class rlbm_domain(ctypes.Structure):
@@ -74,6 +76,8 @@ def load(path=None):
     L.rlbm_status_string.argtypes = [ctypes.c_int]
     L.rlbm_status_string.restype = ctypes.c_char_p
     L.rlbm_last_step_info.argtypes = [_H, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_int)]
+    L.rlbm_step_noalloc.argtypes = [ctypes.POINTER(rlbm_domain), ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint)]
     _lib = L
     return L
 
@@ -194,6 +198,19 @@ class Simulation:
             self.close()
         except Exception:
             pass
+
+
+def step_noalloc(spec, edf, nsteps, f_in, f_out, stream=None, wait=True):
+    """rlbm_step_noalloc: advance one FP64 domain (DomainSpec) by nsteps from the
+    device checkpoint f_in into f_out (torch float64 [72][ny+2][nx+2] on the
+    GPU) using the library's fixed scratch array. Returns this call's warning
+    bits when wait is true (the call then waits for the stream), else None."""
+    dom = make_domains([spec])
+    s = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
+    w = ctypes.c_uint(0)
+    _check(load().rlbm_step_noalloc(dom, edf, nsteps, ctypes.c_void_p(f_in.data_ptr()),
+                                    ctypes.c_void_p(f_out.data_ptr()), s, ctypes.byref(w) if wait else None))
+    return w.value if wait else None
 
 
 def status_string(code):
