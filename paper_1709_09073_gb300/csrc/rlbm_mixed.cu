@@ -340,8 +340,14 @@ __device__ void write_halo_mixed(const DomDev& D, int x, int y, typename S::T* _
   }
 }
 
+#ifndef RLBM_MIXED_MIN_BLOCKS
+// resident 128-thread blocks per SM the register budget must allow: 4 (128 registers)
+// measured fastest on the 2048^2 FP32-deviation case, ahead of 3 (1.13x) and 5 (1.15x)
+#define RLBM_MIXED_MIN_BLOCKS 4
+#endif
+
 template <int EDF, class S>
-__global__ void __launch_bounds__(kThreads) k_step_mixed(StepArgs a) {
+__global__ void __launch_bounds__(kThreads, RLBM_MIXED_MIN_BLOCKS) k_step_mixed(StepArgs a) {
   extern __shared__ float smf[];
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
