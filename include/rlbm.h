@@ -49,10 +49,12 @@ typedef enum { RLBM_MJ = 0, RLBM_FD = 1, RLBM_BE = 2 } rlbm_edf;
  *  RLBM_F64      FP64 populations, FP64 arithmetic throughout (the plain method).
  *  RLBM_F32      FP32 populations; FP32 streaming, equilibrium and relaxation;
  *                moments and Landau solve in FP64-class precision.
- *  RLBM_BF16DEV, RLBM_F16DEV, RLBM_F32DEV
+ *  RLBM_BF16DEV, RLBM_F16DEV
  *                relative deviations h = (f / f_ref - 1) / scale from the rest
  *                equilibrium f_ref(ref_n, ref_theta) of each domain, stored in
- *                BF16, FP16 or FP32; arithmetic as for RLBM_F32. */
+ *                BF16 or FP16; arithmetic as for RLBM_F32.
+ *  RLBM_F32DEV   the deviation f - f_ref itself in FP32 (scale unused);
+ *                arithmetic as for RLBM_F32. */
 typedef enum { RLBM_F64 = 0, RLBM_F32 = 1, RLBM_BF16DEV = 2, RLBM_F16DEV = 3, RLBM_F32DEV = 4 } rlbm_storage;
 
 /* Boundary condition of one side (one ghost layer; Sec. 3):
@@ -73,7 +75,7 @@ typedef struct {
   int bc_xlo, bc_xhi, bc_ylo, bc_yhi;                /* rlbm_bc */
   double t_wall_xlo, t_wall_xhi, t_wall_ylo, t_wall_yhi; /* wall theta, if a wall */
   double ref_n, ref_theta;    /* reference rest equilibrium of the mixed storages */
-  double scale;               /* deviation scale of the *DEV storages (> 0) */
+  double scale;               /* deviation scale of the 16-bit *DEV storages (> 0) */
 } rlbm_domain;
 
 typedef struct {

@@ -1,16 +1,17 @@
 // Mixed-precision step: FP32 / BF16 / FP16 storage, FP32 streaming, equilibrium
 // and relaxation carried out on deviations f - fref from each domain's rest
-// reference equilibrium, and FP64 for the quantities that set conservation:
-// the totals N^mu, T^{mu nu}, the Landau-frame solve (Eq. 21), n and eps, and the
-// degree-1 and degree-2 equilibrium moments.
+// reference equilibrium, and double-float (an unevaluated pair of FP32 numbers,
+// about 48 bits) for the quantities that set conservation: the totals N^mu,
+// T^{mu nu}, the Landau-frame residual (Eq. 21), gamma, n, eps and the degree-1
+// and degree-2 equilibrium moments.
 //
-// GB300 executes FP64 at 1/64 of the FP32 rate, so FP64 is confined to a few
-// dozen operations per cell: the 72-term moment sums run in FP32 on the small
-// deviations (their rounding error is relative to the deviation, not to f),
-// the Landau solve is FP32 Newton followed by two corrections with an FP64
-// residual, and the equilibrium moments that the collision must reproduce
-// exactly for N^0 and T^{mu 0} (Z_1k = n gamma (u_x + i u_y)^k P_1k,
-// Z_2k = eps gamma^2 (u_x + i u_y)^k P_2k) are formed from the FP64 n and eps.
+// GB300 executes FP64 at 1/64 of the FP32 rate, so the kernel issues no FP64
+// instruction: the 72-term moment sums run in FP32 on the small deviations
+// (their rounding error is relative to the deviation, not to f), the Landau
+// solve is FP32 Newton followed by one correction with a double-float residual,
+// and the equilibrium moments that the collision must reproduce exactly for N^0
+// and T^{mu 0} (Z_1k = n gamma (u_x + i u_y)^k P_1k, Z_2k = eps gamma^2
+// (u_x + i u_y)^k P_2k) are formed from the double-float n and eps.
 #include <cuda_runtime.h>
 
 #include "rlbm_dfloat.cuh"
@@ -34,7 +35,15 @@ static __constant__ float c_be_harmf[6];
 static __constant__ float c_g_zcf[6];
 
 constexpr float kPIf = 3.14159265358979f;
+// sqrt(3)/2 = kH + kHl: FP32 value and its residual. Products with sqrt(3)/2
+// take both parts (two FMAs): with kH alone every moment and synthesis that
+// pairs directions at +-30 degrees would shrink by the same 1.8e-8 each step,
+// a steady sink of momentum (a Taylor-Green flow decayed 1e-5 too fast in 500
+// steps).
 constexpr float kH = 0.866025403784438647f;
+constexpr float kHl = (float)(0.866025403784438647 - (double)kH);
+__device__ __forceinline__ float mul_h(float x) { return fmaf(kH, x, kHl * x); }
+__device__ __forceinline__ float fma_h(float x, float y) { return fmaf(kH, x, fmaf(kHl, x, y)); }
 constexpr float kRZCf = (float)RLBM_R_ZC;
 constexpr float kZCf = 0.9999999f;
 
@@ -235,10 +244,10 @@ __device__ __forceinline__ HarmF harmonics_f(const float v[12]) {
   }
   HarmF H;
   H.h0 = ((e[0] + e[1]) + (e[2] + e[3])) + (e[4] + e[5]);
-  H.c1 = fmaf(kH, o[1] - o[5], fmaf(0.5f, o[2] - o[4], o[0]));
-  H.s1 = fmaf(kH, o[2] + o[4], fmaf(0.5f, o[1] + o[5], o[3]));
+  H.c1 = fma_h(o[1] - o[5], fmaf(0.5f, o[2] - o[4], o[0]));
+  H.s1 = fma_h(o[2] + o[4], fmaf(0.5f, o[1] + o[5], o[3]));
   H.c2 = fmaf(0.5f, (e[1] - e[2]) + (e[5] - e[4]), e[0] - e[3]);
-  H.s2 = kH * ((e[1] + e[2]) - (e[4] + e[5]));
+  H.s2 = mul_h((e[1] + e[2]) - (e[4] + e[5]));
   return H;
 }
 
@@ -264,10 +273,10 @@ __device__ __forceinline__ void dfeq_shell(int s, float rres, const float zr[21]
   Rc[0] += rres;
   const float t1 = Rc[0] + Rc[4], t2 = fmaf(-0.5f, Rc[4], Rc[0]), h2 = 0.5f * Rc[2];
   const float Ec0 = t1 + Rc[2], Ec3 = t1 - Rc[2], Ec1 = t2 + h2, Ec2 = t2 - h2;
-  const float Es1 = kH * (Rs[2] + Rs[4]), Es2 = kH * (Rs[2] - Rs[4]);
+  const float Es1 = mul_h(Rs[2] + Rs[4]), Es2 = mul_h(Rs[2] - Rs[4]);
   const float E0 = Ec0, E1 = Ec1 + Es1, E2 = Ec2 + Es2, E3 = Ec3, E4 = Ec2 - Es2, E5 = Ec1 - Es1;
-  const float Oc0 = Rc[1] + Rc[3] + Rc[5], Oc1 = kH * (Rc[1] - Rc[5]), Oc2 = fmaf(0.5f, Rc[1] + Rc[5], -Rc[3]);
-  const float Os1 = fmaf(0.5f, Rs[1] + Rs[5], Rs[3]), Os2 = kH * (Rs[1] - Rs[5]), Os3 = Rs[1] - Rs[3] + Rs[5];
+  const float Oc0 = Rc[1] + Rc[3] + Rc[5], Oc1 = mul_h(Rc[1] - Rc[5]), Oc2 = fmaf(0.5f, Rc[1] + Rc[5], -Rc[3]);
+  const float Os1 = fmaf(0.5f, Rs[1] + Rs[5], Rs[3]), Os2 = mul_h(Rs[1] - Rs[5]), Os3 = Rs[1] - Rs[3] + Rs[5];
   const float O0 = Oc0, O1 = Oc1 + Os1, O2 = Oc2 + Os2, O3 = Os3, O4 = Os2 - Oc2, O5 = Os1 - Oc1;
   fe[0] = E0 + O0; fe[6] = E0 - O0;
   fe[1] = E1 + O1; fe[7] = E1 - O1;
@@ -312,18 +321,25 @@ __device__ __forceinline__ void dz_moments(const DomDev& D, const float g[6], fl
   }
 }
 
-// Halo writer of the mixed step: copies of the cell's deviation (smem column)
-// and, at fixed-T walls, the FP32 equilibrium deviation of the wall ghost.
-template <int EDF, class S>
-__device__ void write_halo_mixed(const DomDev& D, int x, int y, typename S::T* __restrict__ fout, const float* smf,
-                                 int tid, bool have_state, float n, float ux, float uy, float gam, unsigned& st) {
+// Halo writer of the mixed step: copies of the cell's post-collision values
+// (held in its shared-memory column col[q * kThreads]; kEnc: as FP32
+// deviations still to encode, else already encoded) and, at fixed-T walls, the
+// FP32 equilibrium deviation of the wall ghost. Reading the copies back from
+// global memory instead would put a read-after-write round trip to L2 on every
+// edge warp, which costs more than keeping the column up to date.
+template <int EDF, class S, bool kEnc = true>
+__device__ void write_halo_mixed(const DomDev& D, int x, int y, typename S::T* __restrict__ fout, const float* col,
+                                 bool have_state, float n, float ux, float uy, float gam, unsigned& st) {
   int hx[8], hy[8], wall[8];
   const int cnt = halo_targets(D, x, y, hx, hy, wall);
   const long long P = D.plane;
   for (int i = 0; i < cnt; ++i) {
     const long long h = (long long)(hy[i] + 1) * D.pitch + D.lpad + hx[i];
     if (wall[i] < 0 || !have_state) {
-      for (int q = 0; q < 72; ++q) fout[q * P + h] = S::encf(smf[q * kThreads + tid], D, q % 6);
+      for (int q = 0; q < 72; ++q) {
+        if constexpr (kEnc) fout[q * P + h] = S::encf(col[q * kThreads], D, q % 6);
+        else fout[q * P + h] = col[q * kThreads];
+      }
     } else {
       const float tw = (float)D.t_wall[wall[i]];
       float z, g[6];
@@ -346,6 +362,111 @@ __device__ void write_halo_mixed(const DomDev& D, int x, int y, typename S::T* _
 #define RLBM_MIXED_MIN_BLOCKS 4
 #endif
 
+// Collision of one cell (Eqs. 20-25, 10-11 and 3) from its pulled FP32
+// deviations, held in the thread's shared-memory column smf[q * kThreads + tid],
+// and the shell sums A_d = sum_s p_s dv_{6d+s}, B_d = sum_s p_s^2 dv_{6d+s} of
+// each direction; stores f* to fout, writes the cell's halo images and returns
+// its status bits.
+template <int EDF, class S>
+__device__ __forceinline__ unsigned collide_mixed(const DomDev& D, int x, int y, long long c, const float A[12],
+                                                  const float B[12], float* smf, int tid,
+                                                  typename S::T* __restrict__ fout) {
+  const long long P = D.plane;
+  const HarmF ha = harmonics_f(A), hb = harmonics_f(B);
+  // moment totals in double-float: reference moments + FP32 deviation sums
+  const df N0 = df_add(df_make(D.n0_hl[0], D.n0_hl[1]), ha.h0);
+  const df H0 = df_add(df_make(D.t00_hl[0], D.t00_hl[1]), hb.h0);
+  df T[6];
+  T[0] = H0;
+  T[1] = df_make(hb.c1, 0.0f);
+  T[2] = df_make(hb.s1, 0.0f);
+  T[3] = df_scale(df_add(H0, hb.c2), 0.5f);
+  T[4] = df_make(0.5f * hb.s2, 0.0f);
+  T[5] = df_scale(df_add(H0, -hb.c2), 0.5f);
+  df ux, uy, eps, gam;
+  unsigned st = landau_df(T, ux, uy, eps, gam);
+  df n = df_make(0.0f, 0.0f);
+  if (!(st & ST_NONPHYSICAL)) {
+    n = df_mul(gam, df_sub(N0, df_add(df_mul(ux, ha.c1), df_mul(uy, ha.s1))));
+    if (!(n.hi > 0.0f) || !isfinite(n.hi)) st |= ST_NONPHYSICAL;
+  }
+  const bool ok = !(st & ST_NONPHYSICAL);
+  const float uxf = df_to_float(ux), uyf = df_to_float(uy), gf = df_to_float(gam), nf = df_to_float(n);
+  if (ok) {
+    const float ef = df_to_float(eps);
+    float theta, z, g[6];
+    if (EDF == EDF_MJ) {
+      theta = ef / (2.0f * nf);
+      z = nf / (2.0f * kPIf * theta * theta);
+#pragma unroll
+      for (int i = 0; i < 6; ++i) g[i] = z;
+    } else {
+      const float target = 0.5f * kPIf * ef * ef / (nf * nf * nf);
+      const int zs = solve_z_R_f<EDF>(target, z, g);
+      st |= zs;
+      if (zs & ST_CLAMPED) theta = sqrtf(nf / (2.0f * kPIf * g[1]));
+      else theta = 0.5f * g[1] / g[2] * ef / nf;
+    }
+    // conserved equilibrium moments from the double-float state: Z_1k from
+    // n gamma, Z_2k from eps gamma^2 (a clamped BE state relaxes to its own
+    // equilibrium energy 4 pi theta^3 g_3(z_c))
+    const df nG = df_mul(n, gam);
+    df eG2 = df_mul(df_mul(eps, gam), gam);
+    if (st & ST_CLAMPED) eG2 = df_make(4.0f * kPIf * theta * theta * theta * g[2] * gf * gf, 0.0f);
+    float zr[21], zi[21];
+    dz_moments<EDF>(D, g, theta, uxf, uyf, gf, nG.hi, eG2.hi, zr, zi);
+    // Z_20 = eps gamma^2 (1 + u^2/2), all in double-float
+    const df u2h = df_scale(df_add(df_mul(ux, ux), df_mul(uy, uy)), 0.5f);
+    const df dz10 = df_sub(nG, df_make(D.z1_hl[0], D.z1_hl[1]));
+    const df dz20 = df_sub(df_add(eG2, df_mul(eG2, u2h)), df_make(D.z2_hl[0], D.z2_hl[1]));
+    zr[1] = df_to_float(dz10);
+    zr[3] = df_to_float(dz20);
+    // Z_21 = (3/2) eps gamma^2 (u_x + i u_y) (Appendix; the rest state has none),
+    // also from the double-float state rather than from FP32 eps gamma^2
+    const df e15 = df_mul(eG2, 1.5f);
+    zr[4] = df_to_float(df_mul(e15, ux));
+    zi[4] = df_to_float(df_mul(e15, uy));
+    // remove the FP32 tables' defects in N^0, T^00, T^0x, T^0y (FP32 suffices:
+    // the corrections are ~1e-8 of the moments)
+    float d10 = 0.0f, d20 = 0.0f, d21r = 0.0f, d21i = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      d10 = fmaf(c_Ef[EDF][k], zr[k * (k + 1) / 2], d10);
+      d20 = fmaf(c_Ef[EDF][6 + k], zr[k * (k + 1) / 2], d20);
+    }
+#pragma unroll
+    for (int k = 1; k < 6; ++k) {
+      d21r = fmaf(c_Ef[EDF][12 + k], zr[k * (k + 1) / 2 + 1], d21r);
+      d21i = fmaf(c_Ef[EDF][12 + k], zi[k * (k + 1) / 2 + 1], d21i);
+    }
+    zr[1] -= d10;
+    zr[3] -= d20;
+    zr[4] -= d21r;
+    zi[4] -= d21i;
+    const float itau = (float)D.inv_tau;
+    float om[12];
+#pragma unroll
+    for (int d = 0; d < 12; ++d) om[d] = gf * (1.0f - ((float)dcos(d) * uxf + (float)dsin(d) * uyf)) * itau;
+#pragma unroll 1
+    for (int s = 0; s < 6; ++s) {
+      float fe[12];
+      dfeq_shell<EDF>(s, D.rres[s], zr, zi, fe);
+#pragma unroll
+      for (int d = 0; d < 12; ++d) {
+        const int q = 6 * d + s;
+        const float v = smf[q * kThreads + tid];
+        const float r = fmaf(om[d], fe[d] - v, v);
+        smf[q * kThreads + tid] = r;
+        fout[q * P + c] = S::encf(r, D, s);
+      }
+    }
+  } else {
+    for (int q = 0; q < 72; ++q) fout[q * P + c] = S::encf(smf[q * kThreads + tid], D, q % 6);
+  }
+  write_halo_mixed<EDF, S>(D, x, y, fout, smf + tid, ok, nf, uxf, uyf, gf, st);
+  return st;
+}
+
 template <int EDF, class S>
 __global__ void __launch_bounds__(kThreads, RLBM_MIXED_MIN_BLOCKS) k_step_mixed(StepArgs a) {
   extern __shared__ float smf[];
@@ -361,15 +482,20 @@ __global__ void __launch_bounds__(kThreads, RLBM_MIXED_MIN_BLOCKS) k_step_mixed(
     typename S::T* __restrict__ fout = static_cast<typename S::T*>(a.fout) + D.off;
     const long long c = (long long)(y + 1) * W + D.lpad + x;
     // pull (FP32, deviation form) with the FP32 deviation moment sums
-    float A[12], B[12];
+    float A[12], B[12], pc[6], p2c[6];
+#pragma unroll
+    for (int s = 0; s < 6; ++s) {
+      pc[s] = c_pf[EDF][s];
+      p2c[s] = c_p2f[EDF][s];
+    }
 #define RLBM_PULL_DIR(d)                                                        \
   {                                                                             \
     float a_ = 0.0f, b_ = 0.0f;                                                 \
     _Pragma("unroll") for (int s = 0; s < 6; ++s) {                             \
       const float v = S::decf(pull_one<d, float, S>(fin + (6 * d + s) * P, c, W), D, s); \
       smf[(6 * d + s) * kThreads + tid] = v;                                    \
-      a_ = fmaf(v, c_pf[EDF][s], a_);                                           \
-      b_ = fmaf(v, c_p2f[EDF][s], b_);                                          \
+      a_ = fmaf(v, pc[s], a_);                                                  \
+      b_ = fmaf(v, p2c[s], b_);                                                 \
     }                                                                           \
     A[d] = a_;                                                                  \
     B[d] = b_;                                                                  \
@@ -378,93 +504,7 @@ __global__ void __launch_bounds__(kThreads, RLBM_MIXED_MIN_BLOCKS) k_step_mixed(
     RLBM_PULL_DIR(4) RLBM_PULL_DIR(5) RLBM_PULL_DIR(6) RLBM_PULL_DIR(7)
     RLBM_PULL_DIR(8) RLBM_PULL_DIR(9) RLBM_PULL_DIR(10) RLBM_PULL_DIR(11)
 #undef RLBM_PULL_DIR
-    const HarmF ha = harmonics_f(A), hb = harmonics_f(B);
-    // moment totals in double-float: reference moments + FP32 deviation sums
-    const df N0 = df_add(df_make(D.n0_hl[0], D.n0_hl[1]), ha.h0);
-    const df H0 = df_add(df_make(D.t00_hl[0], D.t00_hl[1]), hb.h0);
-    df T[6];
-    T[0] = H0;
-    T[1] = df_make(hb.c1, 0.0f);
-    T[2] = df_make(hb.s1, 0.0f);
-    T[3] = df_scale(df_add(H0, hb.c2), 0.5f);
-    T[4] = df_make(0.5f * hb.s2, 0.0f);
-    T[5] = df_scale(df_add(H0, -hb.c2), 0.5f);
-    df ux, uy, eps, gam;
-    unsigned st = landau_df(T, ux, uy, eps, gam);
-    df n = df_make(0.0f, 0.0f);
-    if (!(st & ST_NONPHYSICAL)) {
-      n = df_mul(gam, df_sub(N0, df_add(df_mul(ux, ha.c1), df_mul(uy, ha.s1))));
-      if (!(n.hi > 0.0f) || !isfinite(n.hi)) st |= ST_NONPHYSICAL;
-    }
-    const bool ok = !(st & ST_NONPHYSICAL);
-    const float uxf = df_to_float(ux), uyf = df_to_float(uy), gf = df_to_float(gam), nf = df_to_float(n);
-    if (ok) {
-      const float ef = df_to_float(eps);
-      float theta, z, g[6];
-      if (EDF == EDF_MJ) {
-        theta = ef / (2.0f * nf);
-        z = nf / (2.0f * kPIf * theta * theta);
-#pragma unroll
-        for (int i = 0; i < 6; ++i) g[i] = z;
-      } else {
-        const float target = 0.5f * kPIf * ef * ef / (nf * nf * nf);
-        const int zs = solve_z_R_f<EDF>(target, z, g);
-        st |= zs;
-        if (zs & ST_CLAMPED) theta = sqrtf(nf / (2.0f * kPIf * g[1]));
-        else theta = 0.5f * g[1] / g[2] * ef / nf;
-      }
-      // conserved equilibrium moments from the double-float state: Z_1k from
-      // n gamma, Z_2k from eps gamma^2 (a clamped BE state relaxes to its own
-      // equilibrium energy 4 pi theta^3 g_3(z_c))
-      const df nG = df_mul(n, gam);
-      df eG2 = df_mul(df_mul(eps, gam), gam);
-      if (st & ST_CLAMPED) eG2 = df_make(4.0f * kPIf * theta * theta * theta * g[2] * gf * gf, 0.0f);
-      float zr[21], zi[21];
-      dz_moments<EDF>(D, g, theta, uxf, uyf, gf, nG.hi, eG2.hi, zr, zi);
-      // Z_20 = eps gamma^2 (1 + u^2/2), all in double-float
-      const df u2h = df_scale(df_add(df_mul(ux, ux), df_mul(uy, uy)), 0.5f);
-      const df dz10 = df_sub(nG, df_make(D.z1_hl[0], D.z1_hl[1]));
-      const df dz20 = df_sub(df_add(eG2, df_mul(eG2, u2h)), df_make(D.z2_hl[0], D.z2_hl[1]));
-      zr[1] = df_to_float(dz10);
-      zr[3] = df_to_float(dz20);
-      // remove the FP32 tables' defects in N^0, T^00, T^0x, T^0y (FP32 suffices:
-      // the corrections are ~1e-8 of the moments)
-      float d10 = 0.0f, d20 = 0.0f, d21r = 0.0f, d21i = 0.0f;
-#pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        d10 = fmaf(c_Ef[EDF][k], zr[k * (k + 1) / 2], d10);
-        d20 = fmaf(c_Ef[EDF][6 + k], zr[k * (k + 1) / 2], d20);
-      }
-#pragma unroll
-      for (int k = 1; k < 6; ++k) {
-        d21r = fmaf(c_Ef[EDF][12 + k], zr[k * (k + 1) / 2 + 1], d21r);
-        d21i = fmaf(c_Ef[EDF][12 + k], zi[k * (k + 1) / 2 + 1], d21i);
-      }
-      zr[1] -= d10;
-      zr[3] -= d20;
-      zr[4] -= d21r;
-      zi[4] -= d21i;
-      const float itau = (float)D.inv_tau;
-      float om[12];
-#pragma unroll
-      for (int d = 0; d < 12; ++d) om[d] = gf * (1.0f - ((float)dcos(d) * uxf + (float)dsin(d) * uyf)) * itau;
-#pragma unroll 1
-      for (int s = 0; s < 6; ++s) {
-        float fe[12];
-        dfeq_shell<EDF>(s, D.rres[s], zr, zi, fe);
-#pragma unroll
-        for (int d = 0; d < 12; ++d) {
-          const int q = 6 * d + s;
-          const float v = smf[q * kThreads + tid];
-          const float r = fmaf(om[d], fe[d] - v, v);
-          smf[q * kThreads + tid] = r;
-          fout[q * P + c] = S::encf(r, D, s);
-        }
-      }
-    } else {
-      for (int q = 0; q < 72; ++q) fout[q * P + c] = S::encf(smf[q * kThreads + tid], D, q % 6);
-    }
-    write_halo_mixed<EDF, S>(D, x, y, fout, smf, tid, ok, nf, uxf, uyf, gf, st);
+    const unsigned st = collide_mixed<EDF, S>(D, x, y, c, A, B, smf, tid, fout);
     if (st) atomicOr(a.status, st);
   }
 }
