@@ -262,6 +262,10 @@ def run_native(args):
                 "hbm_achieved_gbs": round(1152 * cells / (t64 / k64) / 1e9, 1)}
         sim64.close()
 
+    others = None
+    if world == 1 and not args.no_extra:
+        others = run_other_configs(args, hbm_peak)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline(wl, budget_s=args.cpu_seconds)
@@ -280,7 +284,7 @@ def run_native(args):
                            "grid": grid, "l2": "inputs larger than L2 (%.1f GB of populations)"
                            % (2 * 288 * cells / 1e9), "parallelism": "independent domains per GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clocks, "fp64": fp64, "status": status}
+                "clocks": clocks, "fp64": fp64, "other_configs": others, "status": status}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -331,6 +335,40 @@ def run_profile_case(args):
     t = timed_steps(sim, args.steps, torch) if args.steps > 0 else 0.0
     print(json.dumps({"profile_case": args.profile_case, "cells": wl.cells, "status": sim.sync_status(),
                       "steps": args.steps, "mlups": round(wl.cells * args.steps / t / 1e6, 1) if t else None}))
+
+
+def run_other_configs(args, hbm_peak):
+    """The other throughput configurations of the method on this GPU, each with
+    its own autotuned launch: the 8192^2 Bose-Einstein hot spot in FP32
+    deviations and in FP64, and the 64-domain Fermi-Dirac Fourier-flow batch in
+    the 16-bit deviation storages. Device time with CUDA events over K steps
+    after W warm-up steps; inputs exceed L2."""
+    import torch
+    from paper_1709_09073_gb300 import rlbm
+    out = {}
+    cases = [("hot_spot_8192x8192_BE_f32dev", W.hot_spot(L=8192), rlbm.RLBM_F32DEV, 20),
+             ("hot_spot_8192x8192_BE_f64", None, rlbm.RLBM_F64, 4),
+             ("fourier_x64_1024x256_FD_bf16dev", W.batched_fourier(), rlbm.RLBM_BF16DEV, 50),
+             ("fourier_x64_1024x256_FD_f16dev", None, rlbm.RLBM_F16DEV, 50)]
+    wl = None
+    for name, w, storage, k in cases:
+        wl = w if w is not None else wl
+        sim, st = rlbm.from_workload(wl, storage=storage)
+        sim.tune(1)
+        sim.step(3)
+        t = timed_steps(sim, k, torch)
+        st |= sim.sync_status()
+        bpc = BYTES_PER_CELL[storage]
+        ach = bpc * wl.cells / (t / k) / 1e9
+        out[name] = {"value": round(wl.cells * k / t / 1e6, 2), "unit": UNIT, "steps": k,
+                     "ms_per_step": round(t / k * 1e3, 3), "cells": wl.cells, "status": st,
+                     "kernel": "k_step_f64" if storage == rlbm.RLBM_F64 else "k_step_mixed",
+                     "hbm": {"achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
+                             "frac": round(ach / hbm_peak, 4), "algorithmic_bytes_per_cell": bpc}}
+        sim.close()
+        del sim
+        torch.cuda.empty_cache()
+    return out
 
 
 def run_reference(args):
@@ -386,6 +424,8 @@ def main():
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the hot-spot and Fourier-flow configurations")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--profile-case", choices=["mixed", "fp64"], default=None,
                     help="run a small single-domain case for ncu instead of the benchmark")
