@@ -73,6 +73,8 @@ def lib():
         L.orc_expansion_at.restype = ctypes.c_double
         L.orc_moments72.argtypes = [ctypes.c_int, _D, _D, _D]
         L.orc_step.argtypes = [ctypes.POINTER(Domain), _D, _D, _D, _D]
+        L.orc_step_rows.argtypes = [ctypes.POINTER(Domain), _D, _D, _D, _D, _D, _D]
+        L.orc_edge_row.argtypes = [ctypes.POINTER(Domain), _D, _D, ctypes.c_int, _D]
         L.orc_init.argtypes = [ctypes.POINTER(Domain), ctypes.c_int, _D, _D, _D, _D, _D, _D]
         L.orc_fields.argtypes = [ctypes.POINTER(Domain), _D, _D, ctypes.c_int, _D]
         L.orc_num_threads.restype = ctypes.c_int
@@ -171,6 +173,31 @@ def step(dom, f, macro_in=None):
     if st < 0:
         raise ValueError("orc_step rejected its arguments")
     return fo, mo, st
+
+
+def step_rows(dom, f, macro_in, row_lo, row_hi):
+    """One step of a y-slab whose outside rows (y = -1, y = ny; [72][nx + 2] or
+    None for the slab's own boundary condition) come from its neighbours."""
+    nx, ny = dom.nx, dom.ny
+    fo = np.zeros((72, ny, nx))
+    mo = np.zeros((6, ny, nx))
+    mi = _c(macro_in) if macro_in is not None else None
+    lo = _c(row_lo) if row_lo is not None else None
+    hi = _c(row_hi) if row_hi is not None else None
+    st = lib().orc_step_rows(ctypes.byref(dom), _p(_c(f)), _p(mi), _p(lo), _p(hi), _p(fo), _p(mo))
+    if st < 0:
+        raise ValueError("orc_step_rows rejected its arguments")
+    return fo, mo, st
+
+
+def edge_row(dom, f, macro_in, side):
+    """Bottom (side 0) or top (side 1) row as a neighbour reads it, [72][nx + 2]."""
+    row = np.zeros((72, dom.nx + 2))
+    mi = _c(macro_in) if macro_in is not None else None
+    st = lib().orc_edge_row(ctypes.byref(dom), _p(_c(f)), _p(mi), side, _p(row))
+    if st < 0:
+        raise ValueError("orc_edge_row rejected its arguments")
+    return row
 
 
 def run(dom, f, macro, nsteps):

@@ -18,6 +18,8 @@
  *   orc_landau/orc_state   pinned: numpy eigen-decomposition; equilibrium round trip
  *   orc_step               pinned: conservation of N^0, T^{mu 0}; rest state fixed point;
  *                          mirror/rotation symmetry; Taylor-Green viscosity law (Eq. 31)
+ *   orc_step_rows,         pinned: slabs stepped with their neighbours' edge rows equal
+ *   orc_edge_row           orc_step of the whole domain bit for bit
  */
 #include "rlbm_oracle.h"
 
@@ -638,6 +640,7 @@ typedef struct {
   const double *f;
   double *ghost_x; /* [2][ny][72] fixed-T wall ghosts at x = -1, x = nx */
   double *ghost_y; /* [2][nx][72] at y = -1, y = ny */
+  const double *row_lo, *row_hi; /* given rows y = -1, y = ny as [72][nx + 2] (x = -1..nx), or NULL */
 } orc_ctx;
 
 static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
@@ -662,6 +665,9 @@ static double fetch(const orc_ctx *c, int q, int x, int y) {
     else gy = (y < 0) ? -1 : 1;
   }
   int xc = clampi(x, 0, nx - 1), yc = clampi(y, 0, ny - 1);
+  /* a row beyond a slab edge, given by the neighbouring slab (x ghosts included) */
+  const double *row = gy < 0 ? c->row_lo : (gy > 0 ? c->row_hi : NULL);
+  if (row) return row[(size_t)q * (nx + 2) + (gx ? (gx < 0 ? 0 : nx + 1) : xc + 1)];
   if (gx) {
     int bc = gx < 0 ? D->bc_xlo : D->bc_xhi;
     if (bc == ORC_FIXED_T_WALL) return c->ghost_x[((gx < 0 ? 0 : 1) * ny + yc) * 72 + q];
@@ -744,13 +750,13 @@ static int check_domain(const orc_domain *D) {
  * Anderson-Witting relaxation of Eq. (3) with delta t = 1:
  *   f*_i = f_i - gamma (1 - v_i.u) (f_i - f^eq_i) / tau.
  * A cell whose state is non-physical is left unrelaxed and flagged. */
-int orc_step(const orc_domain *D, const double *f_in, const double *macro_in, double *f_out,
-             double *macro_out) {
+static int step_impl(const orc_domain *D, const double *f_in, const double *macro_in, const double *row_lo,
+                     const double *row_hi, double *f_out, double *macro_out) {
   if (check_domain(D)) return -1;
   int nx = D->nx, ny = D->ny, edf = D->edf, st = 0;
   size_t plane = (size_t)nx * ny;
   ensure_gram(edf);
-  orc_ctx c = {D, f_in, NULL, NULL};
+  orc_ctx c = {D, f_in, NULL, NULL, row_lo, row_hi};
   if (has_wall(D)) {
     if (!macro_in) return -1;
     c.ghost_x = (double *)malloc(sizeof(double) * 2 * ny * 72);
@@ -789,6 +795,44 @@ int orc_step(const orc_domain *D, const double *f_in, const double *macro_in, do
         for (int j = 0; j < 6; ++j) macro_out[j * plane + i] = m[j];
     }
   }
+  free(c.ghost_x);
+  free(c.ghost_y);
+  return st;
+}
+
+int orc_step(const orc_domain *D, const double *f_in, const double *macro_in, double *f_out,
+             double *macro_out) {
+  return step_impl(D, f_in, macro_in, NULL, NULL, f_out, macro_out);
+}
+
+/* One step of a slab of a larger domain cut along y: the rows just below and
+ * above the slab (y = -1 and y = ny; NULL = use the slab's own y boundary
+ * condition) are given as [72][nx + 2] arrays of post-collision populations,
+ * x = -1..nx, i.e. with the x ghost values the owning slab computed. Everything
+ * else is orc_step. Used to check a y-slab decomposition against the whole
+ * domain. */
+int orc_step_rows(const orc_domain *D, const double *f_in, const double *macro_in, const double *row_lo,
+                  const double *row_hi, double *f_out, double *macro_out) {
+  return step_impl(D, f_in, macro_in, row_lo, row_hi, f_out, macro_out);
+}
+
+/* Row y = 0 (side 0) or y = ny - 1 (side 1) of the post-collision state as a
+ * neighbouring slab reads it: [72][nx + 2], x = -1..nx, the x ghosts taken from
+ * the x boundary conditions (a wall ghost from macro_in, the pre-collision
+ * state of the edge cell, as in orc_step). */
+int orc_edge_row(const orc_domain *D, const double *f, const double *macro_in, int side, double *row) {
+  if (check_domain(D) || (side != 0 && side != 1)) return -1;
+  int nx = D->nx, ny = D->ny, st = 0;
+  orc_ctx c = {D, f, NULL, NULL, NULL, NULL};
+  if (D->bc_xlo == ORC_FIXED_T_WALL || D->bc_xhi == ORC_FIXED_T_WALL) {
+    if (!macro_in) return -1;
+    c.ghost_x = (double *)malloc(sizeof(double) * 2 * ny * 72);
+    c.ghost_y = (double *)malloc(sizeof(double) * 2 * nx * 72);
+    st |= build_wall_ghosts(D, macro_in, c.ghost_x, c.ghost_y);
+  }
+  int y = side ? ny - 1 : 0;
+  for (int q = 0; q < 72; ++q)
+    for (int x = -1; x <= nx; ++x) row[(size_t)q * (nx + 2) + x + 1] = fetch(&c, q, x, y);
   free(c.ghost_x);
   free(c.ghost_y);
   return st;

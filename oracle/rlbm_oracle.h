@@ -95,6 +95,12 @@ void orc_moments72(int edf, const double f[72], double N[3], double T[6]);
  * (n, theta, ux, uy, z, eps) of the streamed populations, may be NULL. */
 int orc_step(const orc_domain *dom, const double *f_in, const double *macro_in, double *f_out,
              double *macro_out);
+/* y-slab decomposition: a step of a slab whose outside rows ([72][nx + 2],
+ * x = -1..nx, NULL = own boundary condition) are given, and the extraction of
+ * a slab's bottom (side 0) or top (side 1) row as its neighbour reads it. */
+int orc_step_rows(const orc_domain *D, const double *f_in, const double *macro_in, const double *row_lo,
+                  const double *row_hi, double *f_out, double *macro_out);
+int orc_edge_row(const orc_domain *D, const double *f, const double *macro_in, int side, double *row);
 
 /* Initialise f = f^eq from fields a (n or z, per kind), theta, ux, uy.
  * macro_out [3][ny][nx] receives (n, ux, uy), may be NULL. */

@@ -1,0 +1,130 @@
+"""The y-slab decomposition plan (paper_1709_09073_gb300/slabs.py) on CPU:
+slabs stepped by the oracle, each fed only the 30 edge-row planes its
+neighbours send, reproduce the whole-domain oracle bit for bit -- in process
+for three uneven slabs, and as two gloo ranks exchanging rows with
+torch.distributed point-to-point messages."""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+from paper_1709_09073_gb300 import slabs, workloads as W
+
+PERIODIC, ZG, WALL = W.PERIODIC, W.ZERO_GRADIENT, W.FIXED_T_WALL
+CASES = {
+    "periodic": ((PERIODIC,) * 4, (1.0,) * 4),
+    "x_walls": ((WALL, WALL, PERIODIC, PERIODIC), (0.97, 1.04, 1.0, 1.0)),
+    "y_walls_open_x": ((ZG, ZG, WALL, WALL), (1.0, 1.0, 1.03, 0.96)),
+}
+
+
+def test_plan():
+    up, down = slabs.planes_up(), slabs.planes_down()
+    assert len(up) == len(down) == 30 and not set(up) & set(down)
+    for q in up:
+        assert np.sin((q // 6) * np.pi / 6) > 0.1
+    for q in down:
+        assert np.sin((q // 6) * np.pi / 6) < -0.1
+    assert slabs.halo_bytes_per_face(8190, 4) == 983040  # one FP32 face of an 8192-wide domain
+    b = slabs.slab_bounds(11, 3)
+    assert b == [(0, 4), (4, 8), (8, 11)]
+    assert slabs.neighbours(0, 3, False) == (None, 1) and slabs.neighbours(2, 3, True) == (1, 0)
+    with pytest.raises(ValueError):
+        slabs.slab_bounds(2, 3)
+
+
+def _setup(orc, name, nx, ny):
+    bc, tw = CASES[name]
+    spec = W.DomainSpec(nx, ny, 0.85, W.MJ, bc, tw)
+    init = W.random_domain_state(nx, ny, 77, W.MJ, u_amp=0.06)
+    return spec, init
+
+
+def _whole(orc, spec, init, steps):
+    dom = orc.domain(spec.nx, spec.ny, spec.tau, spec.edf, spec.bc, spec.t_wall)
+    f, m, _ = orc.init(dom, init.kind, init.a, init.theta, init.ux, init.uy)
+    f, m, _ = orc.run(dom, f, m, steps)
+    return f
+
+
+class _Slab:
+    def __init__(self, orc, spec, init, rank, nranks):
+        self.orc = orc
+        y0, y1 = slabs.slab_bounds(spec.ny, nranks)[rank]
+        self.y0, self.y1 = y0, y1
+        bc = slabs.slab_bcs(spec.bc, rank, nranks)
+        self.dom = orc.domain(spec.nx, y1 - y0, spec.tau, spec.edf, bc, spec.t_wall)
+        cut = lambda a: np.ascontiguousarray(a[y0:y1])
+        self.f, self.m, _ = orc.init(self.dom, init.kind, cut(init.a), cut(init.theta), cut(init.ux),
+                                     cut(init.uy))
+
+    def edges(self):
+        return self.orc.edge_row(self.dom, self.f, self.m, 0), self.orc.edge_row(self.dom, self.f, self.m, 1)
+
+    def step(self, row_lo, row_hi):
+        self.f, mo, _ = self.orc.step_rows(self.dom, self.f, self.m, row_lo, row_hi)
+        self.m = mo[[0, 2, 3]].copy()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_three_uneven_slabs_in_process(orc, name):
+    nx, ny, steps, k = 14, 11, 6, 3
+    spec, init = _setup(orc, name, nx, ny)
+    periodic_y = spec.bc[2] == PERIODIC
+    parts = [_Slab(orc, spec, init, r, k) for r in range(k)]
+    up, down = slabs.planes_up(), slabs.planes_down()
+    for _ in range(steps):
+        edges = [p.edges() for p in parts]
+        for r, p in enumerate(parts):
+            below, above = slabs.neighbours(r, k, periodic_y)
+            lo = slabs.unpack(slabs.pack(edges[below][1], up), up, nx) if below is not None else None
+            hi = slabs.unpack(slabs.pack(edges[above][0], down), down, nx) if above is not None else None
+            p.step(lo, hi)
+    got = np.concatenate([p.f for p in parts], axis=1)
+    assert np.array_equal(got, _whole(orc, spec, init, steps))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, name, q):
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import torch.distributed as dist
+    from oracle import oracle as orc
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        nx, ny, steps = 12, 10, 5
+        spec, init = _setup(orc, name, nx, ny)
+        part = _Slab(orc, spec, init, rank, world)
+        ex = slabs.SlabExchange(rank, world, nx, spec.bc[2] == PERIODIC)
+        for _ in range(steps):
+            lo, hi = ex.exchange(*part.edges())
+            part.step(lo, hi)
+        q.put((rank, part.y0, part.f))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("name", ["periodic", "x_walls"])
+def test_two_gloo_ranks_match_whole_domain(orc, name):
+    pytest.importorskip("torch")
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, name, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted((q.get(timeout=300) for _ in range(2)), key=lambda r: r[0])
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    got = np.concatenate([r[2] for r in res], axis=1)
+    spec, init = _setup(orc, name, 12, 10)
+    assert np.array_equal(got, _whole(orc, spec, init, 5))
