@@ -259,6 +259,12 @@ def run_native(args):
                              "unit": "TFLOP/s (FP64)", "frac": round(ach / alu_peak, 4),
                              "flops_per_cell": flops_per_cell,
                              "peak_source": "152 SMs x 2 FP64 FMA/clk x median SM clock"},
+                # the pipe issues DADD and DMUL at the DFMA rate but they carry one
+                # flop: the instruction throughput of the FP64 pipe is its real bound
+                "fp64_pipe": {"instr_per_cell": FP64_INSTR_PER_CELL,
+                              "achieved": round(FP64_INSTR_PER_CELL * cells / (t64 / k64) / 1e9, 1),
+                              "peak": round(152 * 2 * clk * 1e6 / 1e9, 1), "unit": "G instr/s",
+                              "frac": round(FP64_INSTR_PER_CELL * cells / (t64 / k64) / (152 * 2 * clk * 1e6), 4)},
                 "hbm_achieved_gbs": round(1152 * cells / (t64 / k64) / 1e9, 1)}
         sim64.close()
 
@@ -274,7 +280,7 @@ def run_native(args):
         line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": round(t / args.steps * 1e3, 4), "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 totals, Landau solve, n, eps)",
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32 (double-float totals, Landau residual, n, eps; no FP64 instruction)",
                 "data": "synthetic",
                 "config": {"workload": wl.name, "domains": len(wl.domains), "cells_per_gpu": cells,
                            "cells_all_ranks": int(total_cells),
@@ -296,6 +302,7 @@ def run_native(args):
 # reports for one 1024^2 launch divided by its cells; used for the FP64 ALU
 # roofline of the plain form.
 FP64_FLOPS_PER_CELL = 2 * 830 + 308 + 202
+FP64_INSTR_PER_CELL = 830 + 308 + 202
 
 
 def cpu_baseline(wl, budget_s=15.0):
