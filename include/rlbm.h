@@ -134,6 +134,15 @@ int rlbm_step(rlbm_handle h, int nsteps);
 int rlbm_moments(rlbm_handle h, int domain, int streamed, double *n, double *theta, double *ux,
                  double *uy, double *z, int on_device);
 
+/* Diagnostic fields of domain `domain` (streamed as for rlbm_moments), FP64
+ * [7][ny][nx] into `out` (host or device per on_device): the heat flux
+ * q^0, q^x, q^y = (3 theta g_3(z) / g_2(z)) (n U^a - N^a) (Sec. 3.3, the
+ * Eckart-Landau correspondence) and the diagonal non-equilibrium tensors
+ * pi^{xx}, pi^{xxx}, pi^{xxxx}, pi^{xxxxx} = sum_i (f_i - f^eq_i) (p_i^x)^k
+ * (Sec. 3.1), f^eq being the fifth-order equilibrium of the cell's Landau
+ * state. Non-physical cells give NaN. Host outputs are complete on return. */
+int rlbm_diagnostics(rlbm_handle h, int domain, int streamed, double *out, int on_device);
+
 /* Raw state of domain `domain` for checkpoint/resume: the stored populations
  * including the one-cell halo ring, as FP64 [72][ny+2][nx+2] (index
  * (q*(ny+2) + y+1)*(nx+2) + x+1 for x in -1..nx, y in -1..ny), converted from

@@ -73,6 +73,7 @@ def lib():
         L.orc_expansion_at.restype = ctypes.c_double
         L.orc_moments72.argtypes = [ctypes.c_int, _D, _D, _D]
         L.orc_step.argtypes = [ctypes.POINTER(Domain), _D, _D, _D, _D]
+        L.orc_diagnostics.argtypes = [ctypes.POINTER(Domain), _D, _D, ctypes.c_int, _D]
         L.orc_step_rows.argtypes = [ctypes.POINTER(Domain), _D, _D, _D, _D, _D, _D]
         L.orc_edge_row.argtypes = [ctypes.POINTER(Domain), _D, _D, ctypes.c_int, _D]
         L.orc_init.argtypes = [ctypes.POINTER(Domain), ctypes.c_int, _D, _D, _D, _D, _D, _D]
@@ -218,6 +219,16 @@ def fields(dom, f, macro_in=None, streamed=True):
     st = lib().orc_fields(ctypes.byref(dom), _p(_c(f)), _p(mi), 1 if streamed else 0, _p(out))
     if st < 0:
         raise ValueError("orc_fields rejected its arguments")
+    return out, st
+
+
+def diagnostics(dom, f, macro_in=None, streamed=True):
+    """[7][ny][nx]: q^0, q^x, q^y, pi^{xx}, pi^{xxx}, pi^{xxxx}, pi^{xxxxx}."""
+    out = np.zeros((7, dom.ny, dom.nx))
+    mi = _c(macro_in) if macro_in is not None else None
+    st = lib().orc_diagnostics(ctypes.byref(dom), _p(_c(f)), _p(mi), 1 if streamed else 0, _p(out))
+    if st < 0:
+        raise ValueError("orc_diagnostics rejected its arguments")
     return out, st
 
 

@@ -18,6 +18,8 @@
  *   orc_landau/orc_state   pinned: numpy eigen-decomposition; equilibrium round trip
  *   orc_step               pinned: conservation of N^0, T^{mu 0}; rest state fixed point;
  *                          mirror/rotation symmetry; Taylor-Green viscosity law (Eq. 31)
+ *   orc_diagnostics        pinned: zero at equilibrium; pi^{x..x} against the Appendix moments;
+ *                          heat flux by the conductivity law kappa = 3 tau g_3 / (2 g_2), Sec. 3.3
  *   orc_step_rows,         pinned: slabs stepped with their neighbours' edge rows equal
  *   orc_edge_row           orc_step of the whole domain bit for bit
  */
@@ -895,6 +897,67 @@ int orc_fields(const orc_domain *D, const double *f_in, const double *macro_in, 
       orc_moments72(edf, f, N, T);
       st |= orc_state(edf, N, T, m);
       for (int j = 0; j < 6; ++j) out[j * plane + i] = m[j];
+    }
+  free(c.ghost_x);
+  free(c.ghost_y);
+  return st;
+}
+
+/* Diagnostic fields [7][ny][nx]: the heat flux of the Eckart-Landau
+ * correspondence (Sec. 3.3), q^a = (3 theta g_3(z) / g_2(z)) (n U^a - N^a),
+ * a = 0, x, y, with U = gamma (1, u_x, u_y); and the diagonal components of
+ * the non-equilibrium tensors of Sec. 3.1, pi^{x..x} = sum_i (f_i - f^eq_i)
+ * (p_i cos phi_i)^k for k = 2..5, f^eq_i being the discrete fifth-order
+ * equilibrium of the cell's Landau state (the one orc_step relaxes towards).
+ * f is pulled first when streamed. Non-physical cells give NaN. */
+int orc_diagnostics(const orc_domain *D, const double *f_in, const double *macro_in, int streamed,
+                    double *out) {
+  if (check_domain(D)) return -1;
+  int nx = D->nx, ny = D->ny, edf = D->edf, st = 0;
+  size_t plane = (size_t)nx * ny;
+  ensure_gram(edf);
+  orc_ctx c = {D, f_in, NULL, NULL, NULL, NULL};
+  if (streamed && has_wall(D)) {
+    if (!macro_in) return -1;
+    c.ghost_x = (double *)malloc(sizeof(double) * 2 * ny * 72);
+    c.ghost_y = (double *)malloc(sizeof(double) * 2 * nx * 72);
+    st |= build_wall_ghosts(D, macro_in, c.ghost_x, c.ghost_y);
+  }
+  double p[6], cphi[12], sphi[12];
+  orc_lattice(edf, p, NULL, cphi, sphi);
+#pragma omp parallel for collapse(2) reduction(| : st) schedule(static)
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x) {
+      double f[72], feq[72], N[3], T[6], m[6], o[7];
+      size_t i = (size_t)y * nx + x;
+      if (streamed) pull_cell(&c, edf, x, y, f);
+      else
+        for (int q = 0; q < 72; ++q) f[q] = f_in[q * plane + i];
+      orc_moments72(edf, f, N, T);
+      int cs = orc_state(edf, N, T, m);
+      st |= cs;
+      if (cs & ORC_E_NONPHYSICAL) {
+        for (int k = 0; k < 7; ++k) o[k] = NAN;
+      } else {
+        double n = m[0], theta = m[1], ux = m[2], uy = m[3], z = m[4];
+        double gamma = 1.0 / sqrt(1.0 - ux * ux - uy * uy);
+        double hq = 3.0 * theta * orc_g(edf, 3, z) / orc_g(edf, 2, z);
+        o[0] = hq * (n * gamma - N[0]);
+        o[1] = hq * (n * gamma * ux - N[1]);
+        o[2] = hq * (n * gamma * uy - N[2]);
+        double eps_eq = (cs & ORC_W_CLAMPED_FUGACITY) ? 4.0 * PI * theta * theta * theta * orc_g(edf, 3, z) : m[5];
+        orc_feq_ne(edf, n, eps_eq, theta, ux, uy, z, feq);
+        for (int k = 2; k <= 5; ++k) {
+          double sum = 0.0;
+          for (int d = 0; d < 12; ++d)
+            for (int s = 0; s < 6; ++s) {
+              int q = 6 * d + s;
+              sum += (f[q] - feq[q]) * pow(p[s] * cphi[d], k);
+            }
+          o[k + 1] = sum;
+        }
+      }
+      for (int k = 0; k < 7; ++k) out[k * plane + i] = o[k];
     }
   free(c.ghost_x);
   free(c.ghost_y);

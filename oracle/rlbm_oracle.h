@@ -112,6 +112,9 @@ int orc_init(const orc_domain *dom, int kind, const double *a, const double *the
  * out: [6][ny][nx] (n, theta, ux, uy, z, eps). */
 int orc_fields(const orc_domain *dom, const double *f, const double *macro_in, int streamed,
                double *out);
+/* heat flux q^0, q^x, q^y and diagonal non-equilibrium tensors of orders 2..5, [7][ny][nx] */
+int orc_diagnostics(const orc_domain *D, const double *f_in, const double *macro_in, int streamed,
+                    double *out);
 
 /* Number of OpenMP threads the oracle uses (1 when built without OpenMP). */
 int orc_num_threads(void);

@@ -327,6 +327,7 @@ int rlbm_moments(rlbm_handle h, int domain, int streamed, double* n, double* the
   const rlbm_domain& d = h->doms[domain];
   const size_t cnt = (size_t)d.nx * d.ny;
   FieldsArgs fa;
+  fa.diag = nullptr;
   fa.doms = h->d_doms;
   fa.dom = domain;
   fa.streamed = streamed ? 1 : 0;
@@ -346,6 +347,33 @@ int rlbm_moments(rlbm_handle h, int domain, int streamed, double* n, double* the
     double* srcs[5] = {fa.n, fa.theta, fa.ux, fa.uy, fa.z};
     for (int k = 0; k < 5 && e == cudaSuccess; ++k)
       if (outs[k]) e = cudaMemcpyAsync(outs[k], srcs[k], cnt * 8, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  }
+  return cuda_fail(e);
+}
+
+int rlbm_diagnostics(rlbm_handle h, int domain, int streamed, double* out, int on_device) {
+  if (!h || domain < 0 || domain >= h->ndom || !out) return RLBM_E_ARG;
+  if (!h->initialized[domain]) return RLBM_E_STATE;
+  const rlbm_domain& d = h->doms[domain];
+  const size_t cnt = (size_t)d.nx * d.ny;
+  FieldsArgs fa;
+  fa.doms = h->d_doms;
+  fa.dom = domain;
+  fa.streamed = streamed ? 1 : 0;
+  fa.f = h->pop[h->cur];
+  fa.status = h->d_status;
+  fa.n = fa.theta = fa.ux = fa.uy = fa.z = nullptr;
+  if (on_device) {
+    fa.diag = out;
+  } else {
+    if (7 * cnt > staging_doubles(h)) return RLBM_E_UNSUPPORTED;
+    fa.diag = staging(h);
+  }
+  cudaError_t e = h->storage == RLBM_F64 ? launch_fields_f64(h->edf, fa, d.nx, d.ny, h->stream)
+                                          : launch_fields_mixed(h->storage, h->edf, fa, d.nx, d.ny, h->stream);
+  if (e == cudaSuccess && !on_device) {
+    e = cudaMemcpyAsync(out, fa.diag, 7 * cnt * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   }
   return cuda_fail(e);

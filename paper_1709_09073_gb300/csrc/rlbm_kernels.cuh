@@ -290,11 +290,50 @@ __global__ void __launch_bounds__(kThreads) k_fields(FieldsArgs a) {
   unsigned st = cell_state<EDF>(N, T, S_);
   const long long i = (long long)y * D.nx + x;
   if (st & ST_NONPHYSICAL) S_.n = S_.theta = S_.ux = S_.uy = S_.z = nan("");
-  a.n[i] = S_.n;
-  a.theta[i] = S_.theta;
-  a.ux[i] = S_.ux;
-  a.uy[i] = S_.uy;
+  if (a.n) a.n[i] = S_.n;
+  if (a.theta) a.theta[i] = S_.theta;
+  if (a.ux) a.ux[i] = S_.ux;
+  if (a.uy) a.uy[i] = S_.uy;
   if (a.z) a.z[i] = S_.z;
+  if (a.diag) {
+    // heat flux q^a = (3 theta g_3 / g_2)(n U^a - N^a), Sec. 3.3, and the
+    // diagonal non-equilibrium tensors pi^{x..x} = sum_i (f_i - f^eq_i) (p_i^x)^k,
+    // k = 2..5 (Sec. 3.1), with f^eq the fifth-order equilibrium of the cell's
+    // Landau state -- the one its next collision relaxes towards
+    const long long np = (long long)D.nx * D.ny;
+    double out[7];
+    if (st & ST_NONPHYSICAL) {
+      for (int k = 0; k < 7; ++k) out[k] = nan("");
+    } else {
+      const double hq = 3.0 * S_.theta * S_.g[2] / S_.g[1];
+      out[0] = hq * (S_.n * S_.gamma - N[0]);
+      out[1] = hq * (S_.n * S_.gamma * S_.ux - N[1]);
+      out[2] = hq * (S_.n * S_.gamma * S_.uy - N[2]);
+      const double eps_eq = (st & ST_CLAMPED) ? 4.0 * PI * S_.theta * S_.theta * S_.theta * S_.g[2] : S_.eps;
+      double zr[21], zi[21];
+      eq_moments<EDF>(S_.g, S_.theta, S_.ux, S_.uy, S_.gamma, S_.n, eps_eq, zr, zi);
+      double p2 = 0.0, p3 = 0.0, p4 = 0.0, p5 = 0.0;
+      for (int s = 0; s < 6; ++s) {
+        double fe[12];
+        feq_shell<EDF>(s, zr, zi, fe);
+#pragma unroll
+        for (int d = 0; d < 12; ++d) {
+          const int q = 6 * d + s;
+          const double v = a.streamed ? sm[q * kThreads + tid] : S::dec((double)S::raw(f[q * P + c]), D, s);
+          const double px = c_p[EDF][s] * dcos(d), w = (v - fe[d]) * px * px;
+          p2 += w;
+          p3 += w * px;
+          p4 += w * px * px;
+          p5 += w * px * px * px;
+        }
+      }
+      out[3] = p2;
+      out[4] = p3;
+      out[5] = p4;
+      out[6] = p5;
+    }
+    for (int k = 0; k < 7; ++k) a.diag[k * np + i] = out[k];
+  }
   if (st) atomicOr(a.status, st);
 }
 

@@ -19,7 +19,8 @@ struct FieldsArgs {
   const DomDev* doms;
   int dom, streamed;
   const void* f;
-  double *n, *theta, *ux, *uy, *z;    // device outputs, z may be null
+  double *n, *theta, *ux, *uy, *z;    // device outputs, each may be null
+  double* diag;                       // null, or [7][ny][nx]: q^0, q^x, q^y, pi^{x..x} orders 2-5
   unsigned* status;
 };
 

@@ -26,7 +26,7 @@ RLBM_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 EXPORTS = ["rlbm_workspace_bytes", "rlbm_create", "rlbm_init", "rlbm_step", "rlbm_moments",
            "rlbm_get_populations", "rlbm_set_populations", "rlbm_tune", "rlbm_sync_status",
-           "rlbm_destroy", "rlbm_status_string", "rlbm_last_step_info", "rlbm_step_noalloc"]
+           "rlbm_destroy", "rlbm_status_string", "rlbm_last_step_info", "rlbm_step_noalloc", "rlbm_diagnostics"]
 
 
 class rlbm_domain(ctypes.Structure):
@@ -71,6 +71,7 @@ def load(path=None):
     L.rlbm_get_populations.argtypes = [_H, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]
     L.rlbm_set_populations.argtypes = [_H, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]
     L.rlbm_tune.argtypes = [_H, ctypes.c_int]
+    L.rlbm_diagnostics.argtypes = [_H, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]
     L.rlbm_sync_status.argtypes = [_H]
     L.rlbm_destroy.argtypes = [_H]
     L.rlbm_status_string.argtypes = [ctypes.c_int]
@@ -165,6 +166,17 @@ class Simulation:
             ptrs = [o.ctypes.data_as(ctypes.c_void_p) for o in outs]
         _check(load().rlbm_moments(self.h, domain, 1 if streamed else 0, *ptrs, 1 if on_device else 0))
         return outs
+
+    DIAGNOSTICS = ("q0", "qx", "qy", "pi2", "pi3", "pi4", "pi5")
+
+    def diagnostics(self, domain, streamed=True):
+        """Heat flux q^0, q^x, q^y and the diagonal non-equilibrium tensors
+        pi^{x..x} of orders 2-5, as a dict of [ny][nx] numpy arrays."""
+        d = self.specs[domain]
+        out = np.empty((7, d.ny, d.nx))
+        _check(load().rlbm_diagnostics(self.h, domain, 1 if streamed else 0,
+                                       out.ctypes.data_as(ctypes.c_void_p), 0))
+        return dict(zip(self.DIAGNOSTICS, out))
 
     def get_populations(self, domain):
         d = self.specs[domain]
