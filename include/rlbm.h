@@ -76,6 +76,9 @@ typedef struct {
   double t_wall_xlo, t_wall_xhi, t_wall_ylo, t_wall_yhi; /* wall theta, if a wall */
   double ref_n, ref_theta;    /* reference rest equilibrium of the mixed storages */
   double scale;               /* deviation scale of the 16-bit *DEV storages (> 0) */
+  double eta_s;               /* > 0: local relaxation time tau = 4 eta_s / theta + 0.2546
+                                 from each cell's temperature (Sec. 3.5; tau above is then
+                                 unused); 0: constant tau */
 } rlbm_domain;
 
 typedef struct {
@@ -83,7 +86,8 @@ typedef struct {
   const rlbm_domain *domains; /* host array of ndomains descriptors (copied) */
   int edf;                    /* rlbm_edf */
   int storage;                /* rlbm_storage */
-  int order;                  /* expansion order of Eq. (10); only 5 is supported */
+  int order;                  /* expansion order N of Eq. (10): 2..5 with RLBM_F64
+                                 storage (Sec. 3.5 order comparison), 5 otherwise */
   void *device_buffer;        /* caller-owned workspace, rlbm_workspace_bytes() */
   size_t buffer_bytes;
   void *cuda_stream;          /* cudaStream_t or NULL */
@@ -185,7 +189,7 @@ int rlbm_last_step_info(rlbm_handle h, long long *cell_updates, int *kernel_laun
  * RLBM_F64) without a handle or workspace and without allocating anything:
  * no cudaMalloc, cudaFree or allocating library routine is called.
  *  - domain: host descriptor, checked as rlbm_create checks it (ref_n,
- *    ref_theta, scale ignored); edf: rlbm_edf.
+ *    ref_theta, scale ignored; eta_s > 0 selects the local tau); edf: rlbm_edf.
  *  - f_in, f_out: caller-owned DEVICE buffers, FP64 [72][ny+2][nx+2] with the
  *    halo ring -- the layout of rlbm_get_populations -- holding the stored
  *    post-collision populations before and after the steps. The halo of f_in

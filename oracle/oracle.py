@@ -44,11 +44,13 @@ class Domain(ctypes.Structure):
                 ("bc_xlo", ctypes.c_int), ("bc_xhi", ctypes.c_int),
                 ("bc_ylo", ctypes.c_int), ("bc_yhi", ctypes.c_int),
                 ("t_wall_xlo", ctypes.c_double), ("t_wall_xhi", ctypes.c_double),
-                ("t_wall_ylo", ctypes.c_double), ("t_wall_yhi", ctypes.c_double)]
+                ("t_wall_ylo", ctypes.c_double), ("t_wall_yhi", ctypes.c_double),
+                ("order", ctypes.c_int), ("eta_s", ctypes.c_double)]
 
 
-def domain(nx, ny, tau, edf, bc=(PERIODIC, PERIODIC, PERIODIC, PERIODIC), t_wall=(1.0, 1.0, 1.0, 1.0)):
-    return Domain(nx, ny, tau, edf, *bc, *t_wall)
+def domain(nx, ny, tau, edf, bc=(PERIODIC, PERIODIC, PERIODIC, PERIODIC), t_wall=(1.0, 1.0, 1.0, 1.0),
+           order=5, eta_s=0.0):
+    return Domain(nx, ny, tau, edf, *bc, *t_wall, order, eta_s)
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -74,6 +76,7 @@ def lib():
         L.orc_moments72.argtypes = [ctypes.c_int, _D, _D, _D]
         L.orc_step.argtypes = [ctypes.POINTER(Domain), _D, _D, _D, _D]
         L.orc_diagnostics.argtypes = [ctypes.POINTER(Domain), _D, _D, ctypes.c_int, _D]
+        L.orc_feq_order.argtypes = [ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 6 + [_D]
         L.orc_step_rows.argtypes = [ctypes.POINTER(Domain), _D, _D, _D, _D, _D, _D]
         L.orc_edge_row.argtypes = [ctypes.POINTER(Domain), _D, _D, ctypes.c_int, _D]
         L.orc_init.argtypes = [ctypes.POINTER(Domain), ctypes.c_int, _D, _D, _D, _D, _D, _D]
@@ -136,6 +139,12 @@ def eq_moments_quad(edf, theta, ux, uy, z):
     M = np.zeros(36)
     lib().orc_eq_moments_quad(edf, theta, ux, uy, z, _p(M))
     return M
+
+
+def feq_order(edf, order, theta, ux, uy, z, n=-1.0, eps=-1.0):
+    f = np.zeros(72)
+    lib().orc_feq_order(edf, order, n, eps, theta, ux, uy, z, _p(f))
+    return f
 
 
 def feq(edf, theta, ux, uy, z):

@@ -20,6 +20,9 @@
  *                          mirror/rotation symmetry; Taylor-Green viscosity law (Eq. 31)
  *   orc_diagnostics        pinned: zero at equilibrium; pi^{x..x} against the Appendix moments;
  *                          heat flux by the conductivity law kappa = 3 tau g_3 / (2 g_2), Sec. 3.3
+ *   orc_feq_order          pinned: moments of degree <= N reproduced; equals the order-N
+ *                          expansion of Fig. 1 (orc_expansion_at) at the nodes
+ *   local tau (eta_s)      pinned: a uniform-theta state equals the constant-tau run
  *   orc_step_rows,         pinned: slabs stepped with their neighbours' edge rows equal
  *   orc_edge_row           orc_step of the whole domain bit for bit
  */
@@ -559,6 +562,63 @@ void orc_feq_ne(int edf, double n, double eps, double theta, double ux, double u
   }
 }
 
+/* Order-N equilibrium (Eq. 10 truncated at N, Sec. 3.5): the same least-squares
+ * projection as orc_feq_ne restricted to the basis functions with n <= N. The
+ * Gram matrix of the retained functions is solved by Gaussian elimination with
+ * partial pivoting, then one refinement step. */
+void orc_feq_order(int edf, int order, double n, double eps, double theta, double ux, double uy, double z,
+                   double feq[72]) {
+  if (order <= 0 || order >= 5) {
+    orc_feq_ne(edf, n, eps, theta, ux, uy, z, feq);
+    return;
+  }
+  ensure_gram(edf);
+  int nb = 0, idx[36];
+  for (int a = 0; a < 36; ++a)
+    if (basis_n[a] <= order) idx[nb++] = a;
+  double M[36], w[6];
+  orc_eq_moments_ne(edf, n, eps, theta, ux, uy, z, M);
+  orc_lattice(edf, NULL, w, NULL, NULL);
+  double G[36][36], A[36][37], c[36] = {0}, r[36];
+  for (int i = 0; i < nb; ++i)
+    for (int j = 0; j < nb; ++j) {
+      double sum = 0.0;
+      for (int q = 0; q < 72; ++q) sum += w[q % 6] * node_phi[edf][q][idx[i]] * node_phi[edf][q][idx[j]];
+      G[i][j] = sum;
+    }
+  for (int pass = 0; pass < 2; ++pass) {
+    /* right-hand side: the moments (pass 0), then the residual M - G c (pass 1) */
+    for (int i = 0; i < nb; ++i) {
+      double rhs = M[idx[i]];
+      if (pass)
+        for (int j = 0; j < nb; ++j) rhs -= G[i][j] * c[j];
+      for (int j = 0; j < nb; ++j) A[i][j] = G[i][j];
+      A[i][nb] = rhs;
+    }
+    for (int col = 0; col < nb; ++col) {
+      int piv = col;
+      for (int rr = col + 1; rr < nb; ++rr)
+        if (fabs(A[rr][col]) > fabs(A[piv][col])) piv = rr;
+      for (int j = 0; j <= nb; ++j) { double t = A[col][j]; A[col][j] = A[piv][j]; A[piv][j] = t; }
+      for (int rr = col + 1; rr < nb; ++rr) {
+        double m = A[rr][col] / A[col][col];
+        for (int j = col; j <= nb; ++j) A[rr][j] -= m * A[col][j];
+      }
+    }
+    for (int i = nb - 1; i >= 0; --i) {
+      double sum = A[i][nb];
+      for (int j = i + 1; j < nb; ++j) sum -= A[i][j] * r[j];
+      r[i] = sum / A[i][i];
+    }
+    for (int i = 0; i < nb; ++i) c[i] += r[i];
+  }
+  for (int q = 0; q < 72; ++q) {
+    double v = 0.0, cv = 0.0;
+    for (int i = 0; i < nb; ++i) neumaier_add(&v, &cv, node_phi[edf][q][idx[i]] * c[i]);
+    feq[q] = w[q % 6] * (v + cv);
+  }
+}
+
 /* Value of the order-N expansion of Eq. (10) at an arbitrary momentum (p, phi):
  * omega(p) times the projection of f^eq/omega onto the polynomials of degree
  * <= N (the basis functions with n <= N), N = 1..5. Used for Fig. 1. */
@@ -716,7 +776,7 @@ static int build_wall_ghosts(const orc_domain *D, const double *macro_in, double
       size_t i = (size_t)y * nx + xb;
       double n = macro_in[i], ux = macro_in[plane + i], uy = macro_in[2 * plane + i], z;
       st |= orc_z_from_n_theta(D->edf, n, tw, &z);
-      orc_feq(D->edf, tw, ux, uy, z, gxs + ((size_t)side * ny + y) * 72);
+      orc_feq_order(D->edf, D->order, -1.0, -1.0, tw, ux, uy, z, gxs + ((size_t)side * ny + y) * 72);
     }
   }
   for (int side = 0; side < 2; ++side) {
@@ -728,7 +788,7 @@ static int build_wall_ghosts(const orc_domain *D, const double *macro_in, double
       size_t i = (size_t)yb * nx + x;
       double n = macro_in[i], ux = macro_in[plane + i], uy = macro_in[2 * plane + i], z;
       st |= orc_z_from_n_theta(D->edf, n, tw, &z);
-      orc_feq(D->edf, tw, ux, uy, z, gys + ((size_t)side * nx + x) * 72);
+      orc_feq_order(D->edf, D->order, -1.0, -1.0, tw, ux, uy, z, gys + ((size_t)side * nx + x) * 72);
     }
   }
   return st;
@@ -783,10 +843,12 @@ static int step_impl(const orc_domain *D, const double *f_in, const double *macr
          * state uses the equilibrium's own eps = 4 pi theta^3 g_3(z_c) */
         double eps_eq = (cs & ORC_W_CLAMPED_FUGACITY)
                             ? 4.0 * PI * m[1] * m[1] * m[1] * orc_g(edf, 3, m[4]) : m[5];
-        orc_feq_ne(edf, m[0], eps_eq, m[1], m[2], m[3], m[4], feq);
+        orc_feq_order(edf, D->order, m[0], eps_eq, m[1], m[2], m[3], m[4], feq);
         double gamma = 1.0 / sqrt(1.0 - m[2] * m[2] - m[3] * m[3]);
+        /* local relaxation time of Sec. 3.5 from the cell's temperature */
+        double tau = D->eta_s > 0.0 ? 4.0 * D->eta_s / m[1] + 0.2546 : D->tau;
         for (int d = 0; d < 12; ++d) {
-          double om = gamma * (1.0 - (cphi[d] * m[2] + sphi[d] * m[3])) / D->tau;
+          double om = gamma * (1.0 - (cphi[d] * m[2] + sphi[d] * m[3])) / tau;
           for (int s = 0; s < 6; ++s) {
             int q = 6 * d + s;
             f_out[q * plane + i] = f[q] - om * (f[q] - feq[q]);
@@ -863,7 +925,7 @@ int orc_init(const orc_domain *D, int kind, const double *a, const double *theta
       if (!(ux[i] * ux[i] + uy[i] * uy[i] < 1.0) || !(theta[i] > 0.0) || !(n > 0.0)) {
         st |= ORC_E_NONPHYSICAL;
       }
-      orc_feq(edf, theta[i], ux[i], uy[i], z, feq);
+      orc_feq_order(edf, D->order, -1.0, -1.0, theta[i], ux[i], uy[i], z, feq);
       for (int q = 0; q < 72; ++q) f[q * plane + i] = feq[q];
       if (macro_out) {
         macro_out[i] = n;
@@ -946,7 +1008,7 @@ int orc_diagnostics(const orc_domain *D, const double *f_in, const double *macro
         o[1] = hq * (n * gamma * ux - N[1]);
         o[2] = hq * (n * gamma * uy - N[2]);
         double eps_eq = (cs & ORC_W_CLAMPED_FUGACITY) ? 4.0 * PI * theta * theta * theta * orc_g(edf, 3, z) : m[5];
-        orc_feq_ne(edf, n, eps_eq, theta, ux, uy, z, feq);
+        orc_feq_order(edf, D->order, n, eps_eq, theta, ux, uy, z, feq);
         for (int k = 2; k <= 5; ++k) {
           double sum = 0.0;
           for (int d = 0; d < 12; ++d)

@@ -40,6 +40,8 @@ typedef struct {
   int edf;
   int bc_xlo, bc_xhi, bc_ylo, bc_yhi; /* periodic must be set on both sides of an axis */
   double t_wall_xlo, t_wall_xhi, t_wall_ylo, t_wall_yhi;
+  int order;    /* expansion order N of Eq. (10), 2..5 (0 is read as 5) */
+  double eta_s; /* > 0: local relaxation time tau = 4 (eta/s) / theta + 0.2546 (Sec. 3.5) */
 } orc_domain;
 
 /* Lattice: shell momenta p[6], per-vector weights w[6] and direction cosines. */
@@ -80,6 +82,11 @@ void orc_feq(int edf, double theta, double ux, double uy, double z, double feq[7
 /* Same with n and eps fixing the degree-1 and degree-2 moments (Eq. 25). */
 void orc_feq_ne(int edf, double n, double eps, double theta, double ux, double uy, double z,
                 double feq[72]);
+
+/* The order-N equilibrium (N = 2..5): projection of f^eq / omega onto the basis
+ * functions of degree <= N only; n or eps < 0 as for orc_eq_moments_ne. */
+void orc_feq_order(int edf, int order, double n, double eps, double theta, double ux, double uy, double z,
+                   double feq[72]);
 
 /* Value of the order-N expansion (N = 1..5) at an arbitrary momentum (Fig. 1). */
 double orc_expansion_at(int edf, int order, double theta, double ux, double uy, double z,

@@ -46,10 +46,11 @@ int validate(const rlbm_config* c) {
   if (!c || c->ndomains < 1 || !c->domains) return RLBM_E_ARG;
   if (c->edf < RLBM_MJ || c->edf > RLBM_BE) return RLBM_E_ARG;
   if (!elem_size(c->storage)) return RLBM_E_ARG;
-  if (c->order != 5) return RLBM_E_UNSUPPORTED;
+  if (c->order < 2 || c->order > 5 || (c->storage != RLBM_F64 && c->order != 5)) return RLBM_E_UNSUPPORTED;
   for (int i = 0; i < c->ndomains; ++i) {
     const rlbm_domain& d = c->domains[i];
     if (d.nx < 1 || d.ny < 1 || !(d.tau > 0.0)) return RLBM_E_ARG;
+    if (!(d.eta_s >= 0.0) || !(d.eta_s < 1e300)) return RLBM_E_ARG;
     if (!valid_bc(d.bc_xlo) || !valid_bc(d.bc_xhi) || !valid_bc(d.bc_ylo) || !valid_bc(d.bc_yhi))
       return RLBM_E_ARG;
     if ((d.bc_xlo == RLBM_PERIODIC) != (d.bc_xhi == RLBM_PERIODIC)) return RLBM_E_ARG;
@@ -90,6 +91,8 @@ void make_layout(const rlbm_config* c, Layout& L) {
     D.ref_n = d.ref_n > 0.0 ? d.ref_n : 1.0;
     D.ref_theta = d.ref_theta > 0.0 ? d.ref_theta : 1.0;
     D.scale = d.scale > 0.0 ? d.scale : 1.0;
+    D.order = c->order;
+    D.eta_s = d.eta_s;
     off = align_up(off + 72 * (size_t)D.plane, kAlign / es);
     for (int y0 = 0; y0 < d.ny; y0 += kTileY)
       for (int x0 = 0; x0 < d.nx; x0 += kTileX) L.tiles.push_back(Tile{i, x0, y0, 0});

@@ -25,10 +25,12 @@ struct DomDev {
   long long plane;        // elements per population plane
   long long off;          // element offset of plane 0 within a population copy
   int bc[4];              // xlo, xhi, ylo, yhi
+  int order, pad_;        // expansion order N of Eq. (10), 2..5
   double inv_tau;
   double t_wall[4];
   double ref_n, ref_theta;  // reference rest equilibrium (deviation form of the mixed path)
   double scale;             // deviation scale of the 16-bit storage
+  double eta_s;             // > 0: local tau = 4 eta_s / theta + 0.2546 (Sec. 3.5); else inv_tau
   // filled on the device from (ref_n, ref_theta) at handle creation:
   double zref[6];           // isotropic equilibrium moments Z_n0 of the reference state
   double n0ref, t00ref;     // N^0 and T^00 of the FP32 reference populations fref

@@ -18,10 +18,21 @@ namespace rlbm {
 static __constant__ double c_p[3][6] = {RLBM_P_MJ_INIT, RLBM_P_FD_INIT, RLBM_P_BE_INIT};
 static __constant__ double c_w[3][6] = {RLBM_W_MJ_INIT, RLBM_W_FD_INIT, RLBM_W_BE_INIT};
 static __constant__ double c_p2[3][6] = {RLBM_P2_MJ_INIT, RLBM_P2_FD_INIT, RLBM_P2_BE_INIT};
-static __constant__ double c_Q[3][126] = {RLBM_Q_MJ_INIT, RLBM_Q_FD_INIT, RLBM_Q_BE_INIT};
+// projection tables per expansion order N = 2..5 (index N - 2; entries of degree
+// above N are zero) and EDF
+static __constant__ double c_Q[4][3][126] = {
+    {RLBM_QO2_MJ_INIT, RLBM_QO2_FD_INIT, RLBM_QO2_BE_INIT},
+    {RLBM_QO3_MJ_INIT, RLBM_QO3_FD_INIT, RLBM_QO3_BE_INIT},
+    {RLBM_QO4_MJ_INIT, RLBM_QO4_FD_INIT, RLBM_QO4_BE_INIT},
+    {RLBM_Q_MJ_INIT, RLBM_Q_FD_INIT, RLBM_Q_BE_INIT}};
 // exact defects of the rounded Q tables in the conserved moments: e1 (N^0, block
 // k = 0), e2 (T^00, block 0), e3 (T^0x + i T^0y, block 1), 6 entries each
-static __constant__ double c_E[3][18] = {RLBM_E_MJ_INIT, RLBM_E_FD_INIT, RLBM_E_BE_INIT};
+static __constant__ double c_E[4][3][18] = {
+    {RLBM_EO2_MJ_INIT, RLBM_EO2_FD_INIT, RLBM_EO2_BE_INIT},
+    {RLBM_EO3_MJ_INIT, RLBM_EO3_FD_INIT, RLBM_EO3_BE_INIT},
+    {RLBM_EO4_MJ_INIT, RLBM_EO4_FD_INIT, RLBM_EO4_BE_INIT},
+    {RLBM_E_MJ_INIT, RLBM_E_FD_INIT, RLBM_E_BE_INIT}};
+constexpr int kOrder5 = 3;  // table index of the fifth order
 static __constant__ double c_pnk[63] = RLBM_PNK_INIT;
 static __constant__ double c_invpow[6 * RLBM_NSERIES] = RLBM_INVPOW_INIT;
 static __constant__ double c_be_exp[6 * RLBM_NEXP] = RLBM_BE_EXP_INIT;
@@ -267,10 +278,11 @@ __device__ int cell_state(const double N[3], const double T[6], CellState& S) {
 // 2 pi 2! g_3 theta^3 = eps (Eq. 25), so that the equilibrium carries the cell's
 // own n and eps exactly and the collision conserves N^0 and T^{mu 0} without a
 // rounding bias from the z, theta round trip.
+// oi selects the expansion order's defect table (order - 2).
 template <int EDF>
 __device__ __forceinline__ void eq_moments(const double g[6], double theta, double ux, double uy,
                                            double gamma, double nA1, double eA2, double zr[21],
-                                           double zi[21]) {
+                                           double zi[21], int oi = kOrder5) {
   const double u2 = ux * ux + uy * uy;
   double wr[6], wi[6];
   wr[0] = 1.0;
@@ -303,13 +315,13 @@ __device__ __forceinline__ void eq_moments(const double g[6], double theta, doub
   double d10 = 0.0, d20 = 0.0, d21r = 0.0, d21i = 0.0;
 #pragma unroll
   for (int n = 0; n < 6; ++n) {
-    d10 = fma(c_E[EDF][n], zr[n * (n + 1) / 2], d10);
-    d20 = fma(c_E[EDF][6 + n], zr[n * (n + 1) / 2], d20);
+    d10 = fma(c_E[oi][EDF][n], zr[n * (n + 1) / 2], d10);
+    d20 = fma(c_E[oi][EDF][6 + n], zr[n * (n + 1) / 2], d20);
   }
 #pragma unroll
   for (int n = 1; n < 6; ++n) {
-    d21r = fma(c_E[EDF][12 + n], zr[n * (n + 1) / 2 + 1], d21r);
-    d21i = fma(c_E[EDF][12 + n], zi[n * (n + 1) / 2 + 1], d21i);
+    d21r = fma(c_E[oi][EDF][12 + n], zr[n * (n + 1) / 2 + 1], d21r);
+    d21i = fma(c_E[oi][EDF][12 + n], zi[n * (n + 1) / 2 + 1], d21i);
   }
   zr[1] -= d10;
   zr[3] -= d20;
@@ -317,21 +329,22 @@ __device__ __forceinline__ void eq_moments(const double g[6], double theta, doub
   zi[4] -= d21i;
 }
 
-// Fifth-order discrete equilibrium of one shell s at the 12 directions:
+// Discrete equilibrium of one shell s at the 12 directions (order index oi =
+// N - 2; the fifth order by default):
 //   f^eq_{ds} = sum_k R^c_k cos(k phi_d) + R^s_k sin(k phi_d),
 //   R^{c|s}_k = sum_{n>=k} Q^(k)_{s n} Re|Im Z_nk,
 // evaluated with the 12-point symmetries phi -> phi + pi (odd k flip sign) and
 // phi -> pi - phi.
 template <int EDF>
 __device__ __forceinline__ void feq_shell(int s, const double zr[21], const double zi[21],
-                                          double fe[12]) {
+                                          double fe[12], int oi = kOrder5) {
   double Rc[6], Rs[6];
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
     double ac = 0.0, as = 0.0;
 #pragma unroll
     for (int n = k; n < 6; ++n) {
-      const double q = c_Q[EDF][qoff(k) + s * (6 - k) + (n - k)];
+      const double q = c_Q[oi][EDF][qoff(k) + s * (6 - k) + (n - k)];
       ac = fma(q, zr[n * (n + 1) / 2 + k], ac);
       as = fma(q, zi[n * (n + 1) / 2 + k], as);
     }

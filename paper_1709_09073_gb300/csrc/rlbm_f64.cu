@@ -28,18 +28,21 @@ __global__ void __launch_bounds__(kThreads) k_step_f64(StepArgs a) {
     unsigned st = cell_state<EDF>(N, T, S);
     const bool ok = !(st & ST_NONPHYSICAL);
     if (ok) {
+      // constant tau, or the local tau = 4 (eta/s) / theta + 0.2546 of Sec. 3.5
+      const double itau = D.eta_s > 0.0 ? 1.0 / (4.0 * D.eta_s / S.theta + 0.2546) : D.inv_tau;
+      const int oi = D.order - 2;
       double om[12];
 #pragma unroll
       for (int d = 0; d < 12; ++d)
-        om[d] = S.gamma * (1.0 - (dcos(d) * S.ux + dsin(d) * S.uy)) * D.inv_tau;
+        om[d] = S.gamma * (1.0 - (dcos(d) * S.ux + dsin(d) * S.uy)) * itau;
       double zr[21], zi[21];
       // a clamped BE state relaxes to its own equilibrium energy 4 pi theta^3 g_3(z_c)
       const double eps_eq = (st & ST_CLAMPED) ? 4.0 * PI * S.theta * S.theta * S.theta * S.g[2] : S.eps;
-      eq_moments<EDF>(S.g, S.theta, S.ux, S.uy, S.gamma, S.n, eps_eq, zr, zi);
+      eq_moments<EDF>(S.g, S.theta, S.ux, S.uy, S.gamma, S.n, eps_eq, zr, zi, oi);
 #pragma unroll 1
       for (int s = 0; s < 6; ++s) {
         double fe[12];
-        feq_shell<EDF>(s, zr, zi, fe);
+        feq_shell<EDF>(s, zr, zi, fe, oi);
 #pragma unroll
         for (int d = 0; d < 12; ++d) {
           const int q = 6 * d + s;

@@ -136,13 +136,13 @@ __device__ __forceinline__ void pull_moments64(const typename S::T* __restrict__
 // FP64 equilibrium at (theta, g, u) written through a functor out(q, value).
 template <int EDF, class Out>
 __device__ __forceinline__ void feq_emit(const double g[6], double theta, double ux, double uy,
-                                         double gamma, Out out) {
+                                         double gamma, int oi, Out out) {
   double zr[21], zi[21];
-  eq_moments<EDF>(g, theta, ux, uy, gamma, -1.0, -1.0, zr, zi);
+  eq_moments<EDF>(g, theta, ux, uy, gamma, -1.0, -1.0, zr, zi, oi);
 #pragma unroll 1
   for (int s = 0; s < 6; ++s) {
     double fe[12];
-    feq_shell<EDF>(s, zr, zi, fe);
+    feq_shell<EDF>(s, zr, zi, fe, oi);
 #pragma unroll
     for (int d = 0; d < 12; ++d) out(6 * d + s, fe[d]);
   }
@@ -206,7 +206,8 @@ __device__ void write_halo64(const DomDev& D, int x, int y, typename S::T* __res
       const double tw = D.t_wall[wall[i]];
       double z, g[6];
       st |= solve_z_from_n_theta<EDF>(n, tw, z, g);
-      feq_emit<EDF>(g, tw, ux, uy, gamma, [&](int q, double v) { fout[q * P + h] = S::enc(v, D, q % 6); });
+      feq_emit<EDF>(g, tw, ux, uy, gamma, D.order - 2,
+                    [&](int q, double v) { fout[q * P + h] = S::enc(v, D, q % 6); });
     }
   }
 }
@@ -239,7 +240,7 @@ __global__ void __launch_bounds__(kThreads) k_init(InitArgs a) {
   const long long c = (long long)(y + 1) * D.pitch + D.lpad + x;
   const long long P = D.plane;
   if (ok) {
-    feq_emit<EDF>(g, theta, ux, uy, gamma, [&](int q, double v) {
+    feq_emit<EDF>(g, theta, ux, uy, gamma, D.order - 2, [&](int q, double v) {
       sm[q * kThreads + tid] = v;
       f[q * P + c] = S::enc(v, D, q % 6);
     });
@@ -311,11 +312,11 @@ __global__ void __launch_bounds__(kThreads) k_fields(FieldsArgs a) {
       out[2] = hq * (S_.n * S_.gamma * S_.uy - N[2]);
       const double eps_eq = (st & ST_CLAMPED) ? 4.0 * PI * S_.theta * S_.theta * S_.theta * S_.g[2] : S_.eps;
       double zr[21], zi[21];
-      eq_moments<EDF>(S_.g, S_.theta, S_.ux, S_.uy, S_.gamma, S_.n, eps_eq, zr, zi);
+      eq_moments<EDF>(S_.g, S_.theta, S_.ux, S_.uy, S_.gamma, S_.n, eps_eq, zr, zi, D.order - 2);
       double p2 = 0.0, p3 = 0.0, p4 = 0.0, p5 = 0.0;
       for (int s = 0; s < 6; ++s) {
         double fe[12];
-        feq_shell<EDF>(s, zr, zi, fe);
+        feq_shell<EDF>(s, zr, zi, fe, D.order - 2);
 #pragma unroll
         for (int d = 0; d < 12; ++d) {
           const int q = 6 * d + s;

@@ -443,7 +443,8 @@ __device__ __forceinline__ unsigned collide_mixed(const DomDev& D, int x, int y,
     zr[3] -= d20;
     zr[4] -= d21r;
     zi[4] -= d21i;
-    const float itau = (float)D.inv_tau;
+    // constant tau, or the local tau = 4 (eta/s) / theta + 0.2546 of Sec. 3.5
+    const float itau = D.eta_s > 0.0 ? 1.0f / (4.0f * (float)D.eta_s / theta + 0.2546f) : (float)D.inv_tau;
     float om[12];
 #pragma unroll
     for (int d = 0; d < 12; ++d) om[d] = gf * (1.0f - ((float)dcos(d) * uxf + (float)dsin(d) * uyf)) * itau;
@@ -526,7 +527,7 @@ __global__ void k_prepare_refs(DomDev* doms, int ndom) {
   double n0 = 0.0, t00 = 0.0;
   for (int s = 0; s < 6; ++s) {
     double fe = 0.0;
-    for (int n = 0; n < 6; ++n) fe += c_Q[EDF][qoff(0) + s * 6 + n] * D.zref[n];
+    for (int n = 0; n < 6; ++n) fe += c_Q[kOrder5][EDF][qoff(0) + s * 6 + n] * D.zref[n];
     const float ff = (float)fe;
     D.fref[s] = ff;
     D.rres[s] = (float)(fe - (double)ff);

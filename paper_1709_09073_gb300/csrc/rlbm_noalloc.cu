@@ -83,6 +83,8 @@ int plan_scratch(const rlbm_domain* d, ScratchPlan& P) {
   D.t_wall[0] = d->t_wall_xlo; D.t_wall[1] = d->t_wall_xhi;
   D.t_wall[2] = d->t_wall_ylo; D.t_wall[3] = d->t_wall_yhi;
   D.ref_n = D.ref_theta = D.scale = 1.0;  // used by the mixed storages only
+  D.order = 5;
+  D.eta_s = d->eta_s > 0.0 ? d->eta_s : 0.0;
   P.tiles_x = (d->nx + kTileW - 1) / kTileW;
   P.ntiles = P.tiles_x * ((d->ny + kTileH - 1) / kTileH);
   size_t b = kAlignB;  // [0, 256): status word

@@ -70,19 +70,28 @@ def radial_rule(edf):
     return roots, w
 
 
-def projection(p, w):
+def projection(p, w, order=NS - 1):
+    """Projection of f^eq / omega onto the basis p^n {cos, sin}(k phi) with
+    k <= n <= order (Eqs. 10-11; order 5 is the full expansion), per harmonic
+    block k: Q[k][s][n - k] = w_s / N_k sum_a p_s^(n_a) (H_k^-1)[a][n - k], H_k the
+    radial Gram matrix of the block. Laid out for order 5 (k, s, n'), the
+    entries of degrees above `order` are zero."""
     Q = []
     for k in range(NS):
-        ns = list(range(k, NS))
-        H = mp.matrix(len(ns), len(ns))
-        for a, na in enumerate(ns):
-            for b, nb in enumerate(ns):
-                H[a, b] = sum(w[s] * p[s] ** (na + nb) for s in range(NS))
-        Hi = H ** -1
+        ns = list(range(k, order + 1))
         Nk = 12 if k == 0 else 6
+        if ns:
+            H = mp.matrix(len(ns), len(ns))
+            for a, na in enumerate(ns):
+                for b, nb in enumerate(ns):
+                    H[a, b] = sum(w[s] * p[s] ** (na + nb) for s in range(NS))
+            Hi = H ** -1
         for s in range(NS):
-            for b in range(len(ns)):
-                Q.append(w[s] / Nk * sum(p[s] ** ns[a] * Hi[a, b] for a in range(len(ns))))
+            for b in range(NS - k):
+                if b < len(ns):
+                    Q.append(w[s] / Nk * sum(p[s] ** ns[a] * Hi[a, b] for a in range(len(ns))))
+                else:
+                    Q.append(mp.mpf(0))
     return Q  # ordered k, s, n'
 
 
@@ -187,6 +196,14 @@ def main():
         hdr.append(c_arr("RLBM_WF_%s" % e, w, "float"))
         hdr.append(c_arr("RLBM_QF_%s" % e, Q, "float"))
         hdr.append(c_arr("RLBM_EF_%s" % e, Ef))
+        # lower expansion orders (Sec. 3.5 order comparison), FP64 path only
+        for order in (2, 3, 4):
+            Qo = projection(p, w, order)
+            Eo = moment_defects(p, Qo, "double")
+            data.setdefault("Qo%d" % order, []).append([float(x) for x in Qo])
+            data.setdefault("Eo%d" % order, []).append(Eo)
+            hdr.append(c_arr("RLBM_QO%d_%s" % (order, e), Qo))
+            hdr.append(c_arr("RLBM_EO%d_%s" % (order, e), Eo))
     polys = moment_polys()
     data["Pnk"] = polys
     hdr.append(c_arr("RLBM_PNK", [c for row in polys for c in row]))

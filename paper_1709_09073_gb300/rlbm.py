@@ -36,7 +36,7 @@ class rlbm_domain(ctypes.Structure):
                 ("t_wall_xlo", ctypes.c_double), ("t_wall_xhi", ctypes.c_double),
                 ("t_wall_ylo", ctypes.c_double), ("t_wall_yhi", ctypes.c_double),
                 ("ref_n", ctypes.c_double), ("ref_theta", ctypes.c_double),
-                ("scale", ctypes.c_double)]
+                ("scale", ctypes.c_double), ("eta_s", ctypes.c_double)]
 
 
 class rlbm_config(ctypes.Structure):
@@ -96,7 +96,7 @@ def _check(code):
 def make_domains(specs):
     arr = (rlbm_domain * len(specs))()
     for i, d in enumerate(specs):
-        arr[i] = rlbm_domain(d.nx, d.ny, d.tau, *d.bc, *d.t_wall, d.ref_n, d.ref_theta, d.scale)
+        arr[i] = rlbm_domain(d.nx, d.ny, d.tau, *d.bc, *d.t_wall, d.ref_n, d.ref_theta, d.scale, d.eta_s)
     return arr
 
 

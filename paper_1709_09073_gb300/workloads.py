@@ -27,6 +27,7 @@ class DomainSpec:
     ref_n: float = 1.0       # reference equilibrium of the deviation storage formats
     ref_theta: float = 1.0
     scale: float = 1.0       # per-domain scale of the deviation storage formats
+    eta_s: float = 0.0       # > 0: local tau = 4 eta_s / theta + 0.2546 (Sec. 3.5)
 
 
 @dataclass
@@ -111,6 +112,23 @@ def hot_spot(L=8192, sigma=64.0, peak=0.5, tau=0.8, steps=2000, edf=BE):
                     [DomainSpec(L, L, tau, edf)],
                     [InitialState(INIT_N_THETA, one, theta, zero, zero.copy())], steps,
                     {"sigma": sigma})
+
+
+def hot_spot_step(L=512, radius=32.0, th_in=1.5, th_out=0.5, eta_s=0.5, steps=100, edf=MJ):
+    """Hot-spot relaxation of the order comparison (Sec. 3.5): n = 1, u = 0,
+    theta = th_in inside the disc of the given radius about the centre and
+    th_out outside; open (zero-gradient) borders; local tau = 4 eta_s / theta
+    + 0.2546."""
+    x, y = _grid(L, L)
+    r2 = (x - L // 2) ** 2 + (y - L // 2) ** 2
+    theta = np.where(r2 <= radius * radius, th_in, th_out).astype(np.float64)
+    one = np.ones((L, L))
+    zero = np.zeros((L, L))
+    zg = (ZERO_GRADIENT,) * 4
+    spec = DomainSpec(L, L, 1.0, edf, zg, eta_s=eta_s)
+    return Workload("hot_spot_step_%dx%d_%s" % (L, L, "MJ FD BE".split()[edf]), [spec],
+                    [InitialState(INIT_N_THETA, one, theta, zero, zero.copy())], steps,
+                    {"radius": radius})
 
 
 def batched_taylor_green(n_domains=256, side_lo=32, side_hi=512, seed=20260101, steps=200,

@@ -67,11 +67,16 @@ def test_workspace_sizing_and_validation(lib_path):
     bad = [W.DomainSpec(8, 8, 0.9, bc=(0, 1, 0, 0))]
     assert rlbm.rlbm_workspace_bytes(bad, rlbm.RLBM_MJ, rlbm.RLBM_F64) == 0
     assert rlbm.rlbm_workspace_bytes([W.DomainSpec(8, 8, -1.0)], 0, 0) == 0
-    assert rlbm.rlbm_workspace_bytes(spec, 0, 0, order=3) == 0
+    # orders 2..5 with FP64 storage; the mixed storages carry the fifth order only
+    assert rlbm.rlbm_workspace_bytes(spec, 0, 0, order=3) > 0
+    assert rlbm.rlbm_workspace_bytes(spec, 0, 0, order=1) == 0
+    assert rlbm.rlbm_workspace_bytes(spec, 0, 0, order=6) == 0
+    assert rlbm.rlbm_workspace_bytes(spec, 0, rlbm.RLBM_F32DEV, order=3) == 0
+    assert rlbm.rlbm_workspace_bytes([W.DomainSpec(8, 8, 0.9, eta_s=-1.0)], 0, 0) == 0
 
 
 def test_struct_layout_matches_header():
     from paper_1709_09073_gb300 import rlbm
-    # rlbm_domain: 2 int + double + 4 int + 4 double + 3 double
-    assert ctypes.sizeof(rlbm.rlbm_domain) == 8 + 8 + 16 + 32 + 24
+    # rlbm_domain: 2 int + double + 4 int + 4 double + 4 double
+    assert ctypes.sizeof(rlbm.rlbm_domain) == 8 + 8 + 16 + 32 + 32
     assert ctypes.sizeof(rlbm.rlbm_config) == 8 + 8 + 12 + 4 + 8 + 8 + 8
