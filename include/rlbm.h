@@ -63,8 +63,13 @@ typedef enum { RLBM_F64 = 0, RLBM_F32 = 1, RLBM_BF16DEV = 2, RLBM_F16DEV = 3, RL
  *  RLBM_FIXED_T_WALL   the ghost holds f^eq(n_b, u_b, theta_wall) with n_b, u_b
  *                      the pre-collision state of the adjacent fluid cell at the
  *                      current time (zeroth-order extrapolation, Sec. 3.3).
+ *  RLBM_VELOCITY_WALL  a wall at rest (Sec. 3.4, Poiseuille flow): the ghost holds
+ *                      f^eq(n_wall, u = 0, theta_wall) plus the non-equilibrium part
+ *                      f* - f^eq of the adjacent fluid cell's last collision
+ *                      (non-equilibrium extrapolation). FP64 storage only; all such
+ *                      sides of a domain share one theta_wall.
  *  At a corner outside both axes an x-side wall takes precedence over a y-side wall. */
-typedef enum { RLBM_PERIODIC = 0, RLBM_ZERO_GRADIENT = 1, RLBM_FIXED_T_WALL = 2 } rlbm_bc;
+typedef enum { RLBM_PERIODIC = 0, RLBM_ZERO_GRADIENT = 1, RLBM_FIXED_T_WALL = 2, RLBM_VELOCITY_WALL = 3 } rlbm_bc;
 
 /* Meaning of the first field given to rlbm_init. */
 typedef enum { RLBM_INIT_N_THETA = 0, RLBM_INIT_Z_THETA = 1 } rlbm_init_kind;
@@ -79,6 +84,9 @@ typedef struct {
   double eta_s;               /* > 0: local relaxation time tau = 4 eta_s / theta + 0.2546
                                  from each cell's temperature (Sec. 3.5; tau above is then
                                  unused); 0: constant tau */
+  double accel_x, accel_y;    /* body acceleration a (Sec. 3.4): the collision relaxes towards
+                                 f^eq at u + a tau; FP64 storage only when non-zero */
+  double n_wall;              /* density of the RLBM_VELOCITY_WALL sides (> 0 if any) */
 } rlbm_domain;
 
 typedef struct {

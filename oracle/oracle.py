@@ -45,12 +45,19 @@ class Domain(ctypes.Structure):
                 ("bc_ylo", ctypes.c_int), ("bc_yhi", ctypes.c_int),
                 ("t_wall_xlo", ctypes.c_double), ("t_wall_xhi", ctypes.c_double),
                 ("t_wall_ylo", ctypes.c_double), ("t_wall_yhi", ctypes.c_double),
-                ("order", ctypes.c_int), ("eta_s", ctypes.c_double)]
+                ("order", ctypes.c_int), ("eta_s", ctypes.c_double),
+                ("accel_x", ctypes.c_double), ("accel_y", ctypes.c_double), ("n_wall", ctypes.c_double)]
+
+VELOCITY_WALL = 3
 
 
 def domain(nx, ny, tau, edf, bc=(PERIODIC, PERIODIC, PERIODIC, PERIODIC), t_wall=(1.0, 1.0, 1.0, 1.0),
-           order=5, eta_s=0.0):
-    return Domain(nx, ny, tau, edf, *bc, *t_wall, order, eta_s)
+           order=5, eta_s=0.0, accel=(0.0, 0.0), n_wall=1.0):
+    return Domain(nx, ny, tau, edf, *bc, *t_wall, order, eta_s, accel[0], accel[1], n_wall)
+
+
+def has_velocity_wall(dom):
+    return VELOCITY_WALL in (dom.bc_xlo, dom.bc_xhi, dom.bc_ylo, dom.bc_yhi)
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -211,13 +218,19 @@ def edge_row(dom, f, macro_in, side):
 
 
 def run(dom, f, macro, nsteps):
-    """Advance nsteps; macro is the (n, ux, uy) pre-collision state used by walls."""
+    """Advance nsteps; macro is the previous state used by walls: (n, ux, uy),
+    or the full 6-plane state when the domain has a velocity wall (a 3-plane
+    macro, as orc_init returns, is then taken as an equilibrium start and
+    completed from the populations)."""
     st_all = 0
     mo = None
+    full = has_velocity_wall(dom)
+    if full and (macro is None or macro.shape[0] != 6):
+        macro, _ = fields(dom, f, None, streamed=False)
     for _ in range(nsteps):
         f, mo, st = step(dom, f, macro)
         st_all |= st
-        macro = mo[[0, 2, 3]].copy()
+        macro = mo.copy() if full else mo[[0, 2, 3]].copy()
     return f, macro, st_all
 
 

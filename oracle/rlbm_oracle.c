@@ -732,11 +732,11 @@ static double fetch(const orc_ctx *c, int q, int x, int y) {
   if (row) return row[(size_t)q * (nx + 2) + (gx ? (gx < 0 ? 0 : nx + 1) : xc + 1)];
   if (gx) {
     int bc = gx < 0 ? D->bc_xlo : D->bc_xhi;
-    if (bc == ORC_FIXED_T_WALL) return c->ghost_x[((gx < 0 ? 0 : 1) * ny + yc) * 72 + q];
+    if (bc >= ORC_FIXED_T_WALL) return c->ghost_x[((gx < 0 ? 0 : 1) * ny + yc) * 72 + q];
   }
   if (gy) {
     int bc = gy < 0 ? D->bc_ylo : D->bc_yhi;
-    if (bc == ORC_FIXED_T_WALL) return c->ghost_y[((gy < 0 ? 0 : 1) * nx + xc) * 72 + q];
+    if (bc >= ORC_FIXED_T_WALL) return c->ghost_y[((gy < 0 ? 0 : 1) * nx + xc) * 72 + q];
   }
   return c->f[((size_t)q * ny + yc) * nx + xc];
 }
@@ -763,40 +763,77 @@ static void pull_cell(const orc_ctx *c, int edf, int x, int y, double f[72]) {
   }
 }
 
-/* Ghost populations of the fixed-T walls from the previous pre-collision state. */
-static int build_wall_ghosts(const orc_domain *D, const double *macro_in, double *gxs, double *gys) {
+static int has_vwall(const orc_domain *D) {
+  return D->bc_xlo == ORC_VELOCITY_WALL || D->bc_xhi == ORC_VELOCITY_WALL ||
+         D->bc_ylo == ORC_VELOCITY_WALL || D->bc_yhi == ORC_VELOCITY_WALL;
+}
+
+/* Relaxation time of a cell: constant, or the local tau of Sec. 3.5. */
+static double cell_tau(const orc_domain *D, double theta) {
+  return D->eta_s > 0.0 ? 4.0 * D->eta_s / theta + 0.2546 : D->tau;
+}
+
+/* The equilibrium a cell relaxes towards: order-N f^eq of its Landau state
+ * (n, eps, theta, z) at the velocity shifted by the body force, u + a tau
+ * (Sec. 3.4; no shift without a force). Also returns the shifted velocity. */
+static void collision_feq(const orc_domain *D, int cs, const double m[6], double feq[72], double *uxe,
+                          double *uye) {
+  int edf = D->edf;
+  double tau = cell_tau(D, m[1]);
+  *uxe = m[2] + D->accel_x * tau;
+  *uye = m[3] + D->accel_y * tau;
+  /* degree-1/2 moments from the cell's n and eps (Eq. 25); a clamped BE state
+   * uses the equilibrium's own eps = 4 pi theta^3 g_3(z_c) */
+  double eps_eq = (cs & ORC_W_CLAMPED_FUGACITY) ? 4.0 * PI * m[1] * m[1] * m[1] * orc_g(edf, 3, m[4]) : m[5];
+  orc_feq_order(edf, D->order, m[0], eps_eq, m[1], *uxe, *uye, m[4], feq);
+}
+
+/* Ghost populations of the walls from the previous step: fixed-T walls from
+ * the pre-collision state (n, u) of the adjacent cell; velocity walls from
+ * f^eq(n_wall, 0, theta_wall) + (f* - f^eq) of the adjacent cell, f* its
+ * post-collision populations (f_in) and f^eq the equilibrium it relaxed
+ * towards, at the force-shifted velocity u + a tau (from its full state in
+ * macro_in). Measured against the shifted equilibrium the wall sits on the
+ * ghost node; against the unshifted one the forcing part of f* - f^eq would
+ * read as a slip (the channel profile's zero moves out by 0.17 cells). */
+static int build_wall_ghosts(const orc_domain *D, const double *macro_in, const double *f_in, double *gxs,
+                             double *gys) {
   int nx = D->nx, ny = D->ny, st = 0;
   size_t plane = (size_t)nx * ny;
-  for (int side = 0; side < 2; ++side) {
-    int bc = side ? D->bc_xhi : D->bc_xlo;
-    if (bc != ORC_FIXED_T_WALL) continue;
-    double tw = side ? D->t_wall_xhi : D->t_wall_xlo;
-    int xb = side ? nx - 1 : 0;
-    for (int y = 0; y < ny; ++y) {
-      size_t i = (size_t)y * nx + xb;
-      double n = macro_in[i], ux = macro_in[plane + i], uy = macro_in[2 * plane + i], z;
-      st |= orc_z_from_n_theta(D->edf, n, tw, &z);
-      orc_feq_order(D->edf, D->order, -1.0, -1.0, tw, ux, uy, z, gxs + ((size_t)side * ny + y) * 72);
+  int full = has_vwall(D);
+  int pn = 0, pux = full ? 2 : 1, puy = full ? 3 : 2;
+  for (int axis = 0; axis < 2; ++axis)
+    for (int side = 0; side < 2; ++side) {
+      int bc = axis == 0 ? (side ? D->bc_xhi : D->bc_xlo) : (side ? D->bc_yhi : D->bc_ylo);
+      if (bc != ORC_FIXED_T_WALL && bc != ORC_VELOCITY_WALL) continue;
+      double tw = axis == 0 ? (side ? D->t_wall_xhi : D->t_wall_xlo) : (side ? D->t_wall_yhi : D->t_wall_ylo);
+      int len = axis == 0 ? ny : nx;
+      double *out = axis == 0 ? gxs : gys;
+      for (int j = 0; j < len; ++j) {
+        int x = axis == 0 ? (side ? nx - 1 : 0) : j, y = axis == 0 ? j : (side ? ny - 1 : 0);
+        size_t i = (size_t)y * nx + x;
+        double *g = out + ((size_t)side * len + j) * 72, z;
+        if (bc == ORC_FIXED_T_WALL) {
+          double n = macro_in[pn * plane + i], ux = macro_in[pux * plane + i], uy = macro_in[puy * plane + i];
+          st |= orc_z_from_n_theta(D->edf, n, tw, &z);
+          orc_feq_order(D->edf, D->order, -1.0, -1.0, tw, ux, uy, z, g);
+        } else {
+          double m[6], feqb[72];
+          for (int k = 0; k < 6; ++k) m[k] = macro_in[k * plane + i];
+          st |= orc_z_from_n_theta(D->edf, D->n_wall, tw, &z);
+          orc_feq_order(D->edf, D->order, -1.0, -1.0, tw, 0.0, 0.0, z, g);
+          double uxe, uye;
+          collision_feq(D, 0, m, feqb, &uxe, &uye);
+          for (int q = 0; q < 72; ++q) g[q] += f_in[q * plane + i] - feqb[q];
+        }
+      }
     }
-  }
-  for (int side = 0; side < 2; ++side) {
-    int bc = side ? D->bc_yhi : D->bc_ylo;
-    if (bc != ORC_FIXED_T_WALL) continue;
-    double tw = side ? D->t_wall_yhi : D->t_wall_ylo;
-    int yb = side ? ny - 1 : 0;
-    for (int x = 0; x < nx; ++x) {
-      size_t i = (size_t)yb * nx + x;
-      double n = macro_in[i], ux = macro_in[plane + i], uy = macro_in[2 * plane + i], z;
-      st |= orc_z_from_n_theta(D->edf, n, tw, &z);
-      orc_feq_order(D->edf, D->order, -1.0, -1.0, tw, ux, uy, z, gys + ((size_t)side * nx + x) * 72);
-    }
-  }
   return st;
 }
 
 static int has_wall(const orc_domain *D) {
-  return D->bc_xlo == ORC_FIXED_T_WALL || D->bc_xhi == ORC_FIXED_T_WALL ||
-         D->bc_ylo == ORC_FIXED_T_WALL || D->bc_yhi == ORC_FIXED_T_WALL;
+  return D->bc_xlo >= ORC_FIXED_T_WALL || D->bc_xhi >= ORC_FIXED_T_WALL ||
+         D->bc_ylo >= ORC_FIXED_T_WALL || D->bc_yhi >= ORC_FIXED_T_WALL;
 }
 
 static int check_domain(const orc_domain *D) {
@@ -823,7 +860,7 @@ static int step_impl(const orc_domain *D, const double *f_in, const double *macr
     if (!macro_in) return -1;
     c.ghost_x = (double *)malloc(sizeof(double) * 2 * ny * 72);
     c.ghost_y = (double *)malloc(sizeof(double) * 2 * nx * 72);
-    st |= build_wall_ghosts(D, macro_in, c.ghost_x, c.ghost_y);
+    st |= build_wall_ghosts(D, macro_in, f_in, c.ghost_x, c.ghost_y);
   }
   double cphi[12], sphi[12];
   orc_lattice(edf, NULL, NULL, cphi, sphi);
@@ -839,16 +876,14 @@ static int step_impl(const orc_domain *D, const double *f_in, const double *macr
       if (cs & ORC_E_NONPHYSICAL) {
         for (int q = 0; q < 72; ++q) f_out[q * plane + i] = f[q];
       } else {
-        /* degree-1/2 moments from the cell's n and eps (Eq. 25); a clamped BE
-         * state uses the equilibrium's own eps = 4 pi theta^3 g_3(z_c) */
-        double eps_eq = (cs & ORC_W_CLAMPED_FUGACITY)
-                            ? 4.0 * PI * m[1] * m[1] * m[1] * orc_g(edf, 3, m[4]) : m[5];
-        orc_feq_order(edf, D->order, m[0], eps_eq, m[1], m[2], m[3], m[4], feq);
-        double gamma = 1.0 / sqrt(1.0 - m[2] * m[2] - m[3] * m[3]);
-        /* local relaxation time of Sec. 3.5 from the cell's temperature */
-        double tau = D->eta_s > 0.0 ? 4.0 * D->eta_s / m[1] + 0.2546 : D->tau;
+        /* the equilibrium of the (force-shifted) state; the local relaxation
+         * time of Sec. 3.5 from the cell's temperature */
+        double uxe, uye;
+        collision_feq(D, cs, m, feq, &uxe, &uye);
+        double gamma = 1.0 / sqrt(1.0 - uxe * uxe - uye * uye);
+        double tau = cell_tau(D, m[1]);
         for (int d = 0; d < 12; ++d) {
-          double om = gamma * (1.0 - (cphi[d] * m[2] + sphi[d] * m[3])) / tau;
+          double om = gamma * (1.0 - (cphi[d] * uxe + sphi[d] * uye)) / tau;
           for (int s = 0; s < 6; ++s) {
             int q = 6 * d + s;
             f_out[q * plane + i] = f[q] - om * (f[q] - feq[q]);
@@ -888,11 +923,11 @@ int orc_edge_row(const orc_domain *D, const double *f, const double *macro_in, i
   if (check_domain(D) || (side != 0 && side != 1)) return -1;
   int nx = D->nx, ny = D->ny, st = 0;
   orc_ctx c = {D, f, NULL, NULL, NULL, NULL};
-  if (D->bc_xlo == ORC_FIXED_T_WALL || D->bc_xhi == ORC_FIXED_T_WALL) {
+  if (D->bc_xlo >= ORC_FIXED_T_WALL || D->bc_xhi >= ORC_FIXED_T_WALL) {
     if (!macro_in) return -1;
     c.ghost_x = (double *)malloc(sizeof(double) * 2 * ny * 72);
     c.ghost_y = (double *)malloc(sizeof(double) * 2 * nx * 72);
-    st |= build_wall_ghosts(D, macro_in, c.ghost_x, c.ghost_y);
+    st |= build_wall_ghosts(D, macro_in, f, c.ghost_x, c.ghost_y);
   }
   int y = side ? ny - 1 : 0;
   for (int q = 0; q < 72; ++q)
@@ -946,7 +981,7 @@ int orc_fields(const orc_domain *D, const double *f_in, const double *macro_in, 
     if (!macro_in) return -1;
     c.ghost_x = (double *)malloc(sizeof(double) * 2 * ny * 72);
     c.ghost_y = (double *)malloc(sizeof(double) * 2 * nx * 72);
-    st |= build_wall_ghosts(D, macro_in, c.ghost_x, c.ghost_y);
+    st |= build_wall_ghosts(D, macro_in, f_in, c.ghost_x, c.ghost_y);
   }
 #pragma omp parallel for collapse(2) reduction(| : st) schedule(static)
   for (int y = 0; y < ny; ++y)
@@ -983,7 +1018,7 @@ int orc_diagnostics(const orc_domain *D, const double *f_in, const double *macro
     if (!macro_in) return -1;
     c.ghost_x = (double *)malloc(sizeof(double) * 2 * ny * 72);
     c.ghost_y = (double *)malloc(sizeof(double) * 2 * nx * 72);
-    st |= build_wall_ghosts(D, macro_in, c.ghost_x, c.ghost_y);
+    st |= build_wall_ghosts(D, macro_in, f_in, c.ghost_x, c.ghost_y);
   }
   double p[6], cphi[12], sphi[12];
   orc_lattice(edf, p, NULL, cphi, sphi);

@@ -25,7 +25,7 @@ extern "C" {
 #define ORC_NBASIS 36
 
 enum { ORC_MJ = 0, ORC_FD = 1, ORC_BE = 2 };
-enum { ORC_PERIODIC = 0, ORC_ZERO_GRADIENT = 1, ORC_FIXED_T_WALL = 2 };
+enum { ORC_PERIODIC = 0, ORC_ZERO_GRADIENT = 1, ORC_FIXED_T_WALL = 2, ORC_VELOCITY_WALL = 3 };
 enum { ORC_INIT_N_THETA = 0, ORC_INIT_Z_THETA = 1 };
 
 /* status bits (OR-ed over cells) */
@@ -42,7 +42,15 @@ typedef struct {
   double t_wall_xlo, t_wall_xhi, t_wall_ylo, t_wall_yhi;
   int order;    /* expansion order N of Eq. (10), 2..5 (0 is read as 5) */
   double eta_s; /* > 0: local relaxation time tau = 4 (eta/s) / theta + 0.2546 (Sec. 3.5) */
+  double accel_x, accel_y; /* body acceleration a: the collision uses u + a tau (Sec. 3.4) */
+  double n_wall;           /* density of ORC_VELOCITY_WALL sides (their theta: t_wall) */
 } orc_domain;
+/* ORC_VELOCITY_WALL (Sec. 3.4, Poiseuille): a wall at rest whose ghost holds
+ * f^eq(n_wall, u = 0, theta_wall) plus the non-equilibrium part f* - f^eq of
+ * the adjacent fluid cell's last collision (f^eq at its force-shifted velocity,
+ * the one it relaxed towards). A domain with such a side passes
+ * orc_step the full previous state (the 6 planes n, theta, ux, uy, z, eps of
+ * orc_step's macro_out) as macro_in instead of (n, ux, uy). */
 
 /* Lattice: shell momenta p[6], per-vector weights w[6] and direction cosines. */
 void orc_lattice(int edf, double p[6], double w[6], double cphi[12], double sphi[12]);

@@ -40,7 +40,9 @@ struct Layout {
   std::vector<Tile> tiles;
 };
 
-bool valid_bc(int b) { return b == RLBM_PERIODIC || b == RLBM_ZERO_GRADIENT || b == RLBM_FIXED_T_WALL; }
+bool valid_bc(int b) {
+  return b == RLBM_PERIODIC || b == RLBM_ZERO_GRADIENT || b == RLBM_FIXED_T_WALL || b == RLBM_VELOCITY_WALL;
+}
 
 int validate(const rlbm_config* c) {
   if (!c || c->ndomains < 1 || !c->domains) return RLBM_E_ARG;
@@ -57,8 +59,19 @@ int validate(const rlbm_config* c) {
     if ((d.bc_ylo == RLBM_PERIODIC) != (d.bc_yhi == RLBM_PERIODIC)) return RLBM_E_ARG;
     const double tw[4] = {d.t_wall_xlo, d.t_wall_xhi, d.t_wall_ylo, d.t_wall_yhi};
     const int bc[4] = {d.bc_xlo, d.bc_xhi, d.bc_ylo, d.bc_yhi};
-    for (int k = 0; k < 4; ++k)
-      if (bc[k] == RLBM_FIXED_T_WALL && !(tw[k] > 0.0)) return RLBM_E_ARG;
+    double tvw = 0.0;
+    bool vw = false;
+    for (int k = 0; k < 4; ++k) {
+      if ((bc[k] == RLBM_FIXED_T_WALL || bc[k] == RLBM_VELOCITY_WALL) && !(tw[k] > 0.0)) return RLBM_E_ARG;
+      if (bc[k] == RLBM_VELOCITY_WALL) {
+        if (vw && tw[k] != tvw) return RLBM_E_ARG;  // one theta_wall for all velocity walls
+        vw = true;
+        tvw = tw[k];
+      }
+    }
+    if (vw && !(d.n_wall > 0.0)) return RLBM_E_ARG;
+    if (!(d.accel_x > -1.0 && d.accel_x < 1.0 && d.accel_y > -1.0 && d.accel_y < 1.0)) return RLBM_E_ARG;
+    if ((vw || d.accel_x != 0.0 || d.accel_y != 0.0) && c->storage != RLBM_F64) return RLBM_E_UNSUPPORTED;
     if (c->storage != RLBM_F64 && (!(d.scale > 0.0) || !(d.ref_n > 0.0) || !(d.ref_theta > 0.0)))
       return RLBM_E_ARG;
     if ((long long)d.nx * d.ny > (1LL << 31)) return RLBM_E_ARG;
@@ -93,6 +106,10 @@ void make_layout(const rlbm_config* c, Layout& L) {
     D.scale = d.scale > 0.0 ? d.scale : 1.0;
     D.order = c->order;
     D.eta_s = d.eta_s;
+    D.tau = d.tau;
+    D.accel_x = d.accel_x;
+    D.accel_y = d.accel_y;
+    D.n_wall = d.n_wall;
     off = align_up(off + 72 * (size_t)D.plane, kAlign / es);
     for (int y0 = 0; y0 < d.ny; y0 += kTileY)
       for (int x0 = 0; x0 < d.nx; x0 += kTileX) L.tiles.push_back(Tile{i, x0, y0, 0});

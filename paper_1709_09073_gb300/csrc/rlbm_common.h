@@ -6,7 +6,7 @@
 namespace rlbm {
 
 enum { EDF_MJ = 0, EDF_FD = 1, EDF_BE = 2 };
-enum { BC_PERIODIC = 0, BC_ZERO_GRADIENT = 1, BC_WALL = 2 };
+enum { BC_PERIODIC = 0, BC_ZERO_GRADIENT = 1, BC_WALL = 2, BC_VWALL = 3 };
 enum { ST_F64 = 0, ST_F32 = 1, ST_BF16DEV = 2, ST_F16DEV = 3, ST_F32DEV = 4 };
 
 // per-cell status bits (identical to the public RLBM_W_* values)
@@ -31,6 +31,9 @@ struct DomDev {
   double ref_n, ref_theta;  // reference rest equilibrium (deviation form of the mixed path)
   double scale;             // deviation scale of the 16-bit storage
   double eta_s;             // > 0: local tau = 4 eta_s / theta + 0.2546 (Sec. 3.5); else inv_tau
+  double tau;               // constant relaxation time (inv_tau = 1 / tau)
+  double accel_x, accel_y;  // body acceleration: the collision uses u + a tau (Sec. 3.4)
+  double n_wall;            // density of the velocity-wall sides
   // filled on the device from (ref_n, ref_theta) at handle creation:
   double zref[6];           // isotropic equilibrium moments Z_n0 of the reference state
   double n0ref, t00ref;     // N^0 and T^00 of the FP32 reference populations fref

@@ -28,17 +28,24 @@ __global__ void __launch_bounds__(kThreads) k_step_f64(StepArgs a) {
     unsigned st = cell_state<EDF>(N, T, S);
     const bool ok = !(st & ST_NONPHYSICAL);
     if (ok) {
-      // constant tau, or the local tau = 4 (eta/s) / theta + 0.2546 of Sec. 3.5
-      const double itau = D.eta_s > 0.0 ? 1.0 / (4.0 * D.eta_s / S.theta + 0.2546) : D.inv_tau;
+      // constant tau, or the local tau = 4 (eta/s) / theta + 0.2546 of Sec. 3.5;
+      // a body force shifts the velocity the collision uses to u + a tau (Sec. 3.4)
+      const double tau = D.eta_s > 0.0 ? 4.0 * D.eta_s / S.theta + 0.2546 : D.tau;
+      const double itau = D.eta_s > 0.0 ? 1.0 / tau : D.inv_tau;
+      double ux = S.ux, uy = S.uy, gam = S.gamma;
+      if (D.accel_x != 0.0 || D.accel_y != 0.0) {
+        ux += D.accel_x * tau;
+        uy += D.accel_y * tau;
+        gam = 1.0 / sqrt(1.0 - ux * ux - uy * uy);
+      }
       const int oi = D.order - 2;
       double om[12];
 #pragma unroll
-      for (int d = 0; d < 12; ++d)
-        om[d] = S.gamma * (1.0 - (dcos(d) * S.ux + dsin(d) * S.uy)) * itau;
+      for (int d = 0; d < 12; ++d) om[d] = gam * (1.0 - (dcos(d) * ux + dsin(d) * uy)) * itau;
       double zr[21], zi[21];
       // a clamped BE state relaxes to its own equilibrium energy 4 pi theta^3 g_3(z_c)
       const double eps_eq = (st & ST_CLAMPED) ? 4.0 * PI * S.theta * S.theta * S.theta * S.g[2] : S.eps;
-      eq_moments<EDF>(S.g, S.theta, S.ux, S.uy, S.gamma, S.n, eps_eq, zr, zi, oi);
+      eq_moments<EDF>(S.g, S.theta, ux, uy, gam, S.n, eps_eq, zr, zi, oi);
 #pragma unroll 1
       for (int s = 0; s < 6; ++s) {
         double fe[12];
@@ -52,10 +59,11 @@ __global__ void __launch_bounds__(kThreads) k_step_f64(StepArgs a) {
           fout[q * P + c] = r;
         }
       }
+      if (touches_vwall(D, x, y)) write_vwall_ghosts<EDF, StoreF64>(D, x, y, fout, sm, tid, &S, &st);
     } else {
       for (int q = 0; q < 72; ++q) fout[q * P + c] = sm[q * kThreads + tid];
     }
-    write_halo64<EDF, StoreF64>(D, x, y, fout, sm, tid, ok, S.n, S.ux, S.uy, S.gamma, st);
+    write_halo64<EDF, StoreF64>(D, x, y, fout, sm, tid, ok, S.n, S.ux, S.uy, S.gamma, st, ok);
     if (st) atomicOr(a.status, st);
   }
 }

@@ -178,10 +178,10 @@ __device__ __forceinline__ int halo_targets(const DomDev& D, int x, int y, int h
       if (i == 0 && j == 0) continue;
       const int tx = xs[i], ty = ys[j];
       int w = -1;
-      if (tx == -1 && D.bc[0] == BC_WALL) w = 0;
-      else if (tx == nx && D.bc[1] == BC_WALL) w = 1;
-      else if (ty == -1 && D.bc[2] == BC_WALL) w = 2;
-      else if (ty == ny && D.bc[3] == BC_WALL) w = 3;
+      if (tx == -1 && D.bc[0] >= BC_WALL) w = 0;
+      else if (tx == nx && D.bc[1] >= BC_WALL) w = 1;
+      else if (ty == -1 && D.bc[2] >= BC_WALL) w = 2;
+      else if (ty == ny && D.bc[3] >= BC_WALL) w = 3;
       hx[cnt] = tx;
       hy[cnt] = ty;
       wall[cnt] = w;
@@ -191,15 +191,27 @@ __device__ __forceinline__ int halo_targets(const DomDev& D, int x, int y, int h
 }
 
 // Halo writer for kernels that hold the cell's populations in FP64 (smem column).
+// Velocity-wall ghosts are skipped when the step has written them already
+// (vw_written); otherwise (initial state, or a cell left unrelaxed) they get the
+// wall equilibrium f^eq(n_wall, 0, theta_wall).
 template <int EDF, class S>
 __device__ void write_halo64(const DomDev& D, int x, int y, typename S::T* __restrict__ fout, const double* sm,
                              int tid, bool have_state, double n, double ux, double uy, double gamma,
-                             unsigned& st) {
+                             unsigned& st, bool vw_written = false) {
   int hx[8], hy[8], wall[8];
   const int cnt = halo_targets(D, x, y, hx, hy, wall);
   const long long P = D.plane;
   for (int i = 0; i < cnt; ++i) {
     const long long h = (long long)(hy[i] + 1) * D.pitch + D.lpad + hx[i];
+    if (wall[i] >= 0 && D.bc[wall[i]] == BC_VWALL) {
+      if (vw_written) continue;
+      const double tw = D.t_wall[wall[i]];
+      double z, g[6];
+      st |= solve_z_from_n_theta<EDF>(D.n_wall, tw, z, g);
+      feq_emit<EDF>(g, tw, 0.0, 0.0, 1.0, D.order - 2,
+                    [&](int q, double v) { fout[q * P + h] = S::enc(v, D, q % 6); });
+      continue;
+    }
     if (wall[i] < 0 || !have_state) {
       for (int q = 0; q < 72; ++q) fout[q * P + h] = S::enc(sm[q * kThreads + tid], D, q % 6);
     } else {
@@ -208,6 +220,56 @@ __device__ void write_halo64(const DomDev& D, int x, int y, typename S::T* __res
       st |= solve_z_from_n_theta<EDF>(n, tw, z, g);
       feq_emit<EDF>(g, tw, ux, uy, gamma, D.order - 2,
                     [&](int q, double v) { fout[q * P + h] = S::enc(v, D, q % 6); });
+    }
+  }
+}
+
+// True when the cell borders a velocity wall (its ghosts need the
+// non-equilibrium extrapolation of the step).
+__device__ __forceinline__ bool touches_vwall(const DomDev& D, int x, int y) {
+  return (x == 0 && D.bc[0] == BC_VWALL) || (x == D.nx - 1 && D.bc[1] == BC_VWALL) ||
+         (y == 0 && D.bc[2] == BC_VWALL) || (y == D.ny - 1 && D.bc[3] == BC_VWALL);
+}
+
+// Velocity-wall ghosts of a cell (Sec. 3.4): f^eq(n_wall, 0, theta_wall) +
+// (f* - f^eq), f* the cell's post-collision populations (smem column) and f^eq
+// the equilibrium it relaxes towards -- its state (n, eps, theta, z) at the
+// force-shifted velocity u + a tau. At the initial state f* is the initial
+// equilibrium. Kept out of line: only edge cells pay for it.
+template <int EDF, class S>
+__device__ __noinline__ void write_vwall_ghosts(const DomDev& D, int x, int y, typename S::T* __restrict__ fout,
+                                                const double* sm, int tid, const CellState* cs, unsigned* st) {
+  int hx[8], hy[8], wall[8];
+  const int cnt = halo_targets(D, x, y, hx, hy, wall);
+  const long long P = D.plane;
+  int tw_side = -1;
+  for (int i = 0; i < cnt; ++i)
+    if (wall[i] >= 0 && D.bc[wall[i]] == BC_VWALL) tw_side = wall[i];
+  if (tw_side < 0) return;
+  const double tw = D.t_wall[tw_side];  // shared by every velocity wall of the domain
+  const int oi = D.order - 2;
+  const double tau = D.eta_s > 0.0 ? 4.0 * D.eta_s / cs->theta + 0.2546 : D.tau;
+  double ux = cs->ux, uy = cs->uy, gam = cs->gamma;
+  if (D.accel_x != 0.0 || D.accel_y != 0.0) {
+    ux += D.accel_x * tau;
+    uy += D.accel_y * tau;
+    gam = 1.0 / sqrt(1.0 - ux * ux - uy * uy);
+  }
+  double z, g[6], zrw[21], ziw[21], zrc[21], zic[21];
+  *st |= solve_z_from_n_theta<EDF>(D.n_wall, tw, z, g);
+  eq_moments<EDF>(g, tw, 0.0, 0.0, 1.0, -1.0, -1.0, zrw, ziw, oi);
+  eq_moments<EDF>(cs->g, cs->theta, ux, uy, gam, cs->n, cs->eps, zrc, zic, oi);
+  for (int s = 0; s < 6; ++s) {
+    double few[12], fe[12];
+    feq_shell<EDF>(s, zrw, ziw, few, oi);
+    feq_shell<EDF>(s, zrc, zic, fe, oi);
+    for (int i = 0; i < cnt; ++i) {
+      if (wall[i] < 0 || D.bc[wall[i]] != BC_VWALL) continue;
+      const long long h = (long long)(hy[i] + 1) * D.pitch + D.lpad + hx[i];
+      for (int d = 0; d < 12; ++d) {
+        const int q = 6 * d + s;
+        fout[q * P + h] = S::enc(few[d] + (sm[q * kThreads + tid] - fe[d]), D, s);
+      }
     }
   }
 }
@@ -250,7 +312,16 @@ __global__ void __launch_bounds__(kThreads) k_init(InitArgs a) {
       f[q * P + c] = S::enc(nan(""), D, q % 6);
     }
   }
-  write_halo64<EDF, S>(D, x, y, f, sm, tid, ok, n, ux, uy, gamma, st);
+  bool vw = false;
+  if (ok && touches_vwall(D, x, y)) {
+    CellState cs;
+    cs.n = n; cs.theta = theta; cs.ux = ux; cs.uy = uy; cs.z = z; cs.gamma = gamma;
+    for (int k = 0; k < 6; ++k) cs.g[k] = g[k];
+    cs.eps = 4.0 * PI * theta * theta * theta * g[2];  // Eq. (25)
+    write_vwall_ghosts<EDF, S>(D, x, y, f, sm, tid, &cs, &st);
+    vw = true;
+  }
+  write_halo64<EDF, S>(D, x, y, f, sm, tid, ok, n, ux, uy, gamma, st, vw);
   if (st) atomicOr(a.status, st);
 }
 

@@ -41,7 +41,9 @@ void* g_scratch_addr[kMaxDevices] = {};  // device address of g_scratch, per dev
 
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-bool bc_ok(int b) { return b == RLBM_PERIODIC || b == RLBM_ZERO_GRADIENT || b == RLBM_FIXED_T_WALL; }
+bool bc_ok(int b) {
+  return b == RLBM_PERIODIC || b == RLBM_ZERO_GRADIENT || b == RLBM_FIXED_T_WALL || b == RLBM_VELOCITY_WALL;
+}
 
 // Offsets (bytes) of the pieces inside g_scratch for one domain.
 struct ScratchPlan {
@@ -58,8 +60,18 @@ int check_domain(const rlbm_domain* d, int edf) {
   if ((d->bc_ylo == RLBM_PERIODIC) != (d->bc_yhi == RLBM_PERIODIC)) return RLBM_E_ARG;
   const int bc[4] = {d->bc_xlo, d->bc_xhi, d->bc_ylo, d->bc_yhi};
   const double tw[4] = {d->t_wall_xlo, d->t_wall_xhi, d->t_wall_ylo, d->t_wall_yhi};
-  for (int k = 0; k < 4; ++k)
-    if (bc[k] == RLBM_FIXED_T_WALL && !(tw[k] > 0.0)) return RLBM_E_ARG;
+  bool vw = false;
+  double tvw = 0.0;
+  for (int k = 0; k < 4; ++k) {
+    if ((bc[k] == RLBM_FIXED_T_WALL || bc[k] == RLBM_VELOCITY_WALL) && !(tw[k] > 0.0)) return RLBM_E_ARG;
+    if (bc[k] == RLBM_VELOCITY_WALL) {
+      if (vw && tw[k] != tvw) return RLBM_E_ARG;
+      vw = true;
+      tvw = tw[k];
+    }
+  }
+  if (vw && !(d->n_wall > 0.0)) return RLBM_E_ARG;
+  if (!(d->accel_x > -1.0 && d->accel_x < 1.0 && d->accel_y > -1.0 && d->accel_y < 1.0)) return RLBM_E_ARG;
   return RLBM_OK;
 }
 
@@ -85,6 +97,10 @@ int plan_scratch(const rlbm_domain* d, ScratchPlan& P) {
   D.ref_n = D.ref_theta = D.scale = 1.0;  // used by the mixed storages only
   D.order = 5;
   D.eta_s = d->eta_s > 0.0 ? d->eta_s : 0.0;
+  D.tau = d->tau;
+  D.accel_x = d->accel_x;
+  D.accel_y = d->accel_y;
+  D.n_wall = d->n_wall;
   P.tiles_x = (d->nx + kTileW - 1) / kTileW;
   P.ntiles = P.tiles_x * ((d->ny + kTileH - 1) / kTileH);
   size_t b = kAlignB;  // [0, 256): status word

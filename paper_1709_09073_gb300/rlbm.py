@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "librlbm.so")
 
 RLBM_MJ, RLBM_FD, RLBM_BE = 0, 1, 2
 RLBM_F64, RLBM_F32, RLBM_BF16DEV, RLBM_F16DEV, RLBM_F32DEV = 0, 1, 2, 3, 4
-RLBM_PERIODIC, RLBM_ZERO_GRADIENT, RLBM_FIXED_T_WALL = 0, 1, 2
+RLBM_PERIODIC, RLBM_ZERO_GRADIENT, RLBM_FIXED_T_WALL, RLBM_VELOCITY_WALL = 0, 1, 2, 3
 RLBM_INIT_N_THETA, RLBM_INIT_Z_THETA = 0, 1
 RLBM_OK = 0
 RLBM_W_LANDAU_MAXITER, RLBM_W_CLAMPED_FUGACITY, RLBM_W_NONPHYSICAL, RLBM_W_ZSOLVE = 1, 2, 4, 8
@@ -36,7 +36,8 @@ class rlbm_domain(ctypes.Structure):
                 ("t_wall_xlo", ctypes.c_double), ("t_wall_xhi", ctypes.c_double),
                 ("t_wall_ylo", ctypes.c_double), ("t_wall_yhi", ctypes.c_double),
                 ("ref_n", ctypes.c_double), ("ref_theta", ctypes.c_double),
-                ("scale", ctypes.c_double), ("eta_s", ctypes.c_double)]
+                ("scale", ctypes.c_double), ("eta_s", ctypes.c_double),
+                ("accel_x", ctypes.c_double), ("accel_y", ctypes.c_double), ("n_wall", ctypes.c_double)]
 
 
 class rlbm_config(ctypes.Structure):
@@ -96,7 +97,8 @@ def _check(code):
 def make_domains(specs):
     arr = (rlbm_domain * len(specs))()
     for i, d in enumerate(specs):
-        arr[i] = rlbm_domain(d.nx, d.ny, d.tau, *d.bc, *d.t_wall, d.ref_n, d.ref_theta, d.scale, d.eta_s)
+        arr[i] = rlbm_domain(d.nx, d.ny, d.tau, *d.bc, *d.t_wall, d.ref_n, d.ref_theta, d.scale, d.eta_s,
+                             d.accel[0], d.accel[1], d.n_wall)
     return arr
 
 

@@ -11,7 +11,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 MJ, FD, BE = 0, 1, 2
-PERIODIC, ZERO_GRADIENT, FIXED_T_WALL = 0, 1, 2
+PERIODIC, ZERO_GRADIENT, FIXED_T_WALL, VELOCITY_WALL = 0, 1, 2, 3
 INIT_N_THETA, INIT_Z_THETA = 0, 1
 Z_C = 1.0 - 1.0e-7  # BE reference fugacity, Eq. (15)
 
@@ -28,6 +28,8 @@ class DomainSpec:
     ref_theta: float = 1.0
     scale: float = 1.0       # per-domain scale of the deviation storage formats
     eta_s: float = 0.0       # > 0: local tau = 4 eta_s / theta + 0.2546 (Sec. 3.5)
+    accel: tuple = (0.0, 0.0)  # body acceleration (Sec. 3.4 forcing)
+    n_wall: float = 1.0      # density of velocity walls
 
 
 @dataclass

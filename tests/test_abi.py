@@ -73,10 +73,17 @@ def test_workspace_sizing_and_validation(lib_path):
     assert rlbm.rlbm_workspace_bytes(spec, 0, 0, order=6) == 0
     assert rlbm.rlbm_workspace_bytes(spec, 0, rlbm.RLBM_F32DEV, order=3) == 0
     assert rlbm.rlbm_workspace_bytes([W.DomainSpec(8, 8, 0.9, eta_s=-1.0)], 0, 0) == 0
+    # velocity walls and body forces: FP64 storage, one wall temperature, a wall density
+    vw = (W.PERIODIC, W.PERIODIC, W.VELOCITY_WALL, W.VELOCITY_WALL)
+    assert rlbm.rlbm_workspace_bytes([W.DomainSpec(4, 8, 3.0, bc=vw, accel=(1e-8, 0.0))], 0, 0) > 0
+    assert rlbm.rlbm_workspace_bytes([W.DomainSpec(4, 8, 3.0, bc=vw)], 0, rlbm.RLBM_F32DEV) == 0
+    assert rlbm.rlbm_workspace_bytes([W.DomainSpec(4, 8, 3.0, accel=(1e-8, 0.0))], 0, rlbm.RLBM_F32DEV) == 0
+    assert rlbm.rlbm_workspace_bytes([W.DomainSpec(4, 8, 3.0, bc=vw, t_wall=(1, 1, 1.0, 1.1))], 0, 0) == 0
+    assert rlbm.rlbm_workspace_bytes([W.DomainSpec(4, 8, 3.0, bc=vw, n_wall=0.0)], 0, 0) == 0
 
 
 def test_struct_layout_matches_header():
     from paper_1709_09073_gb300 import rlbm
-    # rlbm_domain: 2 int + double + 4 int + 4 double + 4 double
-    assert ctypes.sizeof(rlbm.rlbm_domain) == 8 + 8 + 16 + 32 + 32
+    # rlbm_domain: 2 int + double + 4 int + 4 double + 7 double
+    assert ctypes.sizeof(rlbm.rlbm_domain) == 8 + 8 + 16 + 32 + 56
     assert ctypes.sizeof(rlbm.rlbm_config) == 8 + 8 + 12 + 4 + 8 + 8 + 8

@@ -1,0 +1,69 @@
+"""Velocity walls (non-equilibrium extrapolation) and the body force of the
+Poiseuille flow (Sec. 3.4) on the FP64 CUDA path against the oracle, 1e-12
+(n, theta relative; u normwise): a transient with random fields, and the
+forced channel flow run to its steady parabola (its velocity, ~4e-7 c, is
+checked to an absolute 1e-14: FP64 resolves momentum to ~1e-16 of T^00)."""
+import numpy as np
+import pytest
+
+from paper_1709_09073_gb300 import workloads as W
+from test_gpu_fp64 import errors
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def R():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_1709_09073_gb300 import build, rlbm
+    build.build()
+    rlbm.load()
+    return rlbm
+
+
+def _pair(R, orc, spec, init, steps):
+    sim = R.Simulation([spec], edf=spec.edf, storage=R.RLBM_F64)
+    st = sim.init(0, init)
+    sim.step(steps)
+    out = sim.moments(0)
+    st |= sim.sync_status()
+    sim.close()
+    dom = orc.domain(spec.nx, spec.ny, spec.tau, spec.edf, spec.bc, spec.t_wall, accel=spec.accel,
+                     n_wall=spec.n_wall)
+    f, m, _ = orc.init(dom, init.kind, init.a, init.theta, init.ux, init.uy)
+    f, m, _ = orc.run(dom, f, m, steps)
+    ref, _ = orc.fields(dom, f, m, streamed=True)
+    return out, ref, st
+
+
+@pytest.mark.parametrize("edf", [0, 1, 2])
+@pytest.mark.parametrize("bc", [(W.PERIODIC, W.PERIODIC, W.VELOCITY_WALL, W.VELOCITY_WALL),
+                                (W.VELOCITY_WALL, W.VELOCITY_WALL, W.VELOCITY_WALL, W.VELOCITY_WALL),
+                                (W.VELOCITY_WALL, W.ZERO_GRADIENT, W.PERIODIC, W.PERIODIC)])
+def test_velocity_walls_and_force_transient(R, orc, edf, bc):
+    spec = W.DomainSpec(37, 11, 0.9, edf, bc, (1.02, 1.02, 1.02, 1.02), accel=(2e-4, -1e-4), n_wall=1.05)
+    init = W.random_domain_state(37, 11, 70 + edf, edf, u_amp=0.05)
+    out, ref, st = _pair(R, orc, spec, init, 15)
+    errs = errors(out, ref)
+    print("vwall edf %d bc %s: n %.2e theta %.2e u %.2e" % ((edf, bc) + tuple(errs[:3])))
+    assert (st & R.RLBM_W_NONPHYSICAL) == 0
+    assert max(errs[:3]) <= 1e-12, errs
+
+
+def test_poiseuille_steady_state(R, orc):
+    tau, ny = 3.0, 15
+    nu = (tau - 0.2546) / 4
+    spec = W.DomainSpec(1, ny, tau, W.MJ, (W.PERIODIC, W.PERIODIC, W.VELOCITY_WALL, W.VELOCITY_WALL),
+                        accel=(1e-8, 0.0), n_wall=1.0)
+    one, zero = np.ones((ny, 1)), np.zeros((ny, 1))
+    init = W.InitialState(W.INIT_N_THETA, one, one, zero, zero.copy())
+    out, ref, st = _pair(R, orc, spec, init, int(12 * (ny + 1) ** 2 / nu))
+    assert st == 0
+    # the flow is slow (u ~ 4e-7 c): FP64 resolves the momentum only to ~1e-16 of
+    # T^00 ~ 2, so the bound is absolute at that floor, not relative to u
+    du = np.max(np.abs(out[2] - ref[2]))
+    print("poiseuille ny %d: |du| %.2e of max u %.2e" % (ny, du, np.max(np.abs(ref[2]))))
+    assert du <= 1e-14
+    assert max(errors(out, ref)[:2]) <= 1e-12

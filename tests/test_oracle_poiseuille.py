@@ -1,0 +1,56 @@
+"""Pins of the body force and the velocity wall (Sec. 3.4, Poiseuille flow) in
+the oracle: a uniform fluid under acceleration a gains velocity a per step
+(Newton's law for the u + a tau momentum update); a fluid at rest between
+velocity walls at its own density and temperature stays at rest; the forced
+channel flow reaches a steady parabola that vanishes at the wall nodes (the
+ghost rows) with a curvature giving the Taylor-Green viscosity law
+nu = (tau - 0.2546) / 4 to within 2 %."""
+import numpy as np
+import pytest
+
+from paper_1709_09073_gb300 import workloads as W
+
+VW = (W.PERIODIC, W.PERIODIC, W.VELOCITY_WALL, W.VELOCITY_WALL)
+
+
+@pytest.mark.parametrize("edf", [0, 1])
+def test_uniform_acceleration(orc, edf):
+    a = (1e-8, -2e-8)
+    dom = orc.domain(4, 4, 1.3, edf, accel=a)
+    one, zero = np.ones((4, 4)), np.zeros((4, 4))
+    f, m, _ = orc.init(dom, 0, one, one, zero, zero)
+    f, m, _ = orc.run(dom, f, m, 40)
+    fl, _ = orc.fields(dom, f, m, True)
+    assert abs(fl[2].mean() / (40 * a[0]) - 1.0) <= 1e-6
+    assert abs(fl[3].mean() / (40 * a[1]) - 1.0) <= 1e-6
+
+
+@pytest.mark.parametrize("edf", [0, 2])
+def test_rest_between_velocity_walls(orc, edf):
+    th = 1.1
+    n = 0.8
+    dom = orc.domain(5, 6, 0.9, edf, VW, (1.0, 1.0, th, th), n_wall=n)
+    f, m, _ = orc.init(dom, 0, n * np.ones((6, 5)), th * np.ones((6, 5)), np.zeros((6, 5)), np.zeros((6, 5)))
+    f, m, _ = orc.run(dom, f, m, 30)
+    fl, _ = orc.fields(dom, f, m, True)
+    assert np.max(np.abs(fl[2:4])) <= 1e-15
+    assert np.max(np.abs(fl[0] / n - 1.0)) <= 1e-13 and np.max(np.abs(fl[1] / th - 1.0)) <= 1e-13
+
+
+def test_poiseuille_parabola(orc):
+    tau, a, ny = 3.0, 1e-8, 23
+    nu = (tau - 0.2546) / 4
+    dom = orc.domain(1, ny, tau, 0, VW, accel=(a, 0.0), n_wall=1.0)
+    one, zero = np.ones((ny, 1)), np.zeros((ny, 1))
+    f, m, _ = orc.init(dom, 0, one, one, zero, zero)
+    f, m, _ = orc.run(dom, f, m, int(12 * (ny + 1) ** 2 / nu))
+    ux = orc.fields(dom, f, m, False)[0][2][:, 0]
+    f2, m2, _ = orc.run(dom, f, m, 200)
+    assert np.max(np.abs(orc.fields(dom, f2, m2, False)[0][2][:, 0] - ux)) <= 1e-9 * ux.max()  # steady
+    y = np.arange(ny, dtype=float)
+    c = np.polyfit(y, ux, 2)
+    assert np.max(np.abs(np.polyval(c, y) - ux)) <= 1e-3 * ux.max()   # a parabola
+    lo, hi = np.sort(np.roots(c))
+    assert abs(lo + 1.0) <= 0.05 and abs(hi - ny) <= 0.05           # zero at the wall nodes
+    assert abs(-a / (2 * c[0]) / nu - 1.0) <= 0.02                    # curvature a / (2 nu)
+    assert np.allclose(ux, ux[::-1], rtol=1e-12, atol=0)              # symmetric channel
