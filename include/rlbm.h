@@ -108,6 +108,8 @@ typedef struct {
 #define RLBM_W_NONPHYSICAL 4        /* some cell had |u|>=1, n<=0, eps<=0 or a non-finite
                                        moment; it was streamed but not relaxed */
 #define RLBM_W_ZSOLVE 8             /* fugacity solve (FD/BE) did not converge in some cell */
+#define RLBM_W_DEVICE_TIMEOUT 16    /* a bounded wait inside a kernel gave up (a copy did not
+                                       arrive within a second); that step's results are invalid */
 #define RLBM_E_ARG (-1)             /* invalid argument */
 #define RLBM_E_CUDA (-2)            /* a CUDA call failed */
 #define RLBM_E_STATE (-3)           /* call out of order (e.g. step before init) */
@@ -164,12 +166,31 @@ int rlbm_get_populations(rlbm_handle h, int domain, double *f, int on_device);
 int rlbm_set_populations(rlbm_handle h, int domain, const double *f, int on_device);
 
 /* Autotune the launch of the step kernel on the current state (left unchanged):
- * time `repeats` launches of each candidate grid -- one block per 32 x 4 tile,
- * or a persistent grid of k x (SM count) blocks, k in {1, 2, 3, 4, 6, 8} -- and
- * keep the fastest for later rlbm_step calls (the captured step graphs are
- * rebuilt). Every domain must be initialised. Returns the chosen grid size
- * (> 0) or an error; device warnings raised while timing are discarded. */
+ * time `repeats` launches of each candidate -- every kernel variant the handle
+ * has (rlbm_select_kernel) with one block per 32 x 4 tile or a persistent grid
+ * of k x (SM count) blocks, k in {1, 2, 3, 4, 6, 8} -- and keep the fastest for
+ * later rlbm_step calls (the captured step graphs are rebuilt). Every domain
+ * must be initialised. Returns the chosen grid size (> 0) or an error; device
+ * warnings raised while timing are discarded. */
 int rlbm_tune(rlbm_handle h, int repeats);
+
+/* Variants of the mixed-precision step kernel; both compute the same update
+ * with the same arithmetic (identical results).
+ *  RLBM_KERNEL_L1   each thread pulls its bilinear neighbours from global
+ *                   memory through L1 and stores its 72 values (default);
+ *  RLBM_KERNEL_TMA  a ring of TMA boxes (one direction's six shell planes of a
+ *                   32 x 4 tile and its ring) staged in shared memory; FP32
+ *                   storages also write the collided tile back with one bulk
+ *                   tensor store. Needs the driver's tensor-map encoder and
+ *                   domains at least 4 cells wide. */
+#define RLBM_KERNEL_L1 0
+#define RLBM_KERNEL_TMA 1
+
+/* Select the step kernel variant (kernel >= 0) or query it (kernel < 0).
+ * Returns the variant now in use, RLBM_E_ARG for an unknown variant, or
+ * RLBM_E_UNSUPPORTED for RLBM_KERNEL_TMA on FP64 storage or without TMA
+ * descriptors. rlbm_tune may change the selection. */
+int rlbm_select_kernel(rlbm_handle h, int kernel);
 
 /* Wait for the handle's stream, return the warning bits accumulated since the
  * last call (and clear them), or RLBM_E_CUDA. */

@@ -1,5 +1,7 @@
 // Host side of the C ABI declared in include/rlbm.h: workspace layout, handle,
 // CUDA-graph replay of the step, host/device transfers and status handling.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -34,7 +36,7 @@ size_t elem_size(int storage) {
 
 struct Layout {
   size_t esize = 0;
-  size_t status_off = 0, doms_off = 0, tiles_off = 0, pop_off[2] = {0, 0};
+  size_t status_off = 0, doms_off = 0, tiles_off = 0, tmaps_off = 0, pop_off[2] = {0, 0};
   size_t pop_elems = 0, pop_bytes = 0, total = 0;
   std::vector<DomDev> dd;
   std::vector<Tile> tiles;
@@ -123,6 +125,9 @@ void make_layout(const rlbm_config* c, Layout& L) {
   b = align_up(b + sizeof(DomDev) * L.dd.size(), kAlign);
   L.tiles_off = b;
   b = align_up(b + sizeof(Tile) * L.tiles.size(), kAlign);
+  // TMA descriptors of the staged mixed step: [kind (load, store)][copy][domain]
+  L.tmaps_off = b;
+  if (c->storage != RLBM_F64) b = align_up(b + 4 * (size_t)kTensorMapBytes * L.dd.size(), kAlign);
   L.pop_off[0] = b;
   b += L.pop_bytes;
   L.pop_off[1] = b;
@@ -142,6 +147,7 @@ struct rlbm_ctx {
   unsigned* d_status = nullptr;
   DomDev* d_doms = nullptr;
   Tile* d_tiles = nullptr;
+  unsigned char* d_tmaps = nullptr;  // null unless the TMA-staged variant is available
   void* pop[2] = {nullptr, nullptr};
   int cur = 0;
   std::vector<char> initialized;
@@ -152,6 +158,7 @@ struct rlbm_ctx {
   int last_launches = 0;
   long long cells = 0;
   int grid = 0;                  // blocks of the step kernel (0 = one per tile)
+  int kernel = RLBM_KERNEL_L1;   // mixed step variant (rlbm_select_kernel)
 };
 
 namespace {
@@ -166,6 +173,11 @@ cudaError_t launch_step(rlbm_ctx* h, int from) {
   a.fin = h->pop[from];
   a.fout = h->pop[1 - from];
   a.status = h->d_status;
+  // descriptors [kind][copy][domain]: loads of copy `from`, stores into the other copy
+  const size_t per = (size_t)h->ndom * kTensorMapBytes;
+  const bool tma = h->d_tmaps && h->kernel == RLBM_KERNEL_TMA;
+  a.tmaps = tma ? h->d_tmaps + (size_t)from * per : nullptr;
+  a.tmaps_out = tma && h->L.esize == 4 ? h->d_tmaps + (size_t)(2 + 1 - from) * per : nullptr;
   const int grid = h->grid > 0 ? h->grid : a.ntiles;
   if (h->storage == RLBM_F64) return launch_step_f64(h->edf, a, grid, h->stream);
   return launch_step_mixed(h->storage, h->edf, a, grid, h->stream);
@@ -192,6 +204,68 @@ cudaError_t capture(rlbm_ctx* h, int from, int nsteps, cudaGraphExec_t* out) {
   e = cudaGraphInstantiate(out, g, 0);
   cudaGraphDestroy(g);
   return e;
+}
+
+// TMA descriptors of the staged mixed step, written into `out` as
+// [kind][copy][domain]:
+//  kind 0 (load): a 3D tensor {pitch, ny + 2, 72} of the copy's elements (rows
+//    and planes as laid out, halo included), boxes of tma_box_width x 6 rows x
+//    6 planes, zero fill outside;
+//  kind 1 (store, FP32 storages): the interior cells {nx & ~3, ny, 72} of the
+//    copy, boxes of one 32 x 4 tile x 72 planes. Writes outside the tensor are
+//    clipped, but along x only at 16-byte granularity: a width that is not a
+//    multiple of 4 cells would let a store spill into the halo column x = nx,
+//    so the last nx % 4 cells of each row are stored by their threads instead.
+// Returns false if the driver offers no encoder or refuses a descriptor (or a
+// domain is narrower than 4 cells); the handle then has only the L1 variant.
+bool encode_tmaps(const rlbm_ctx* h, std::vector<unsigned char>& out) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+      cudaGetLastError();  // clear the non-sticky error the failed query recorded
+      return false;
+    }
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const size_t es = h->L.esize;
+  const size_t nd = (size_t)h->ndom;
+  out.assign(4 * (size_t)kTensorMapBytes * nd, 0);
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const CUtensorMapDataType dt = es == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
+  for (int copy = 0; copy < 2; ++copy)
+    for (size_t i = 0; i < nd; ++i) {
+      const DomDev& D = h->L.dd[i];
+      char* plane0 = static_cast<char*>(h->pop[copy]) + (size_t)D.off * es;
+      const cuuint64_t strides[2] = {(cuuint64_t)D.pitch * es, (cuuint64_t)D.plane * es};
+      CUtensorMap* ml = reinterpret_cast<CUtensorMap*>(out.data() + ((0 * 2 + copy) * nd + i) * kTensorMapBytes);
+      const cuuint64_t dl[3] = {(cuuint64_t)D.pitch, (cuuint64_t)D.ny + 2, 72};
+      const cuuint32_t bl[3] = {(cuuint32_t)tma_box_width((int)es), (cuuint32_t)kBoxRows, 6};
+      if (encode(ml, dt, 3, plane0, dl, strides, bl, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+      if (es != 4) continue;
+      if (D.nx < 4) return false;
+      CUtensorMap* ms = reinterpret_cast<CUtensorMap*>(out.data() + ((1 * 2 + copy) * nd + i) * kTensorMapBytes);
+      char* cell00 = plane0 + ((size_t)D.pitch + (size_t)D.lpad) * es;  // cell (0, 0), 16-byte aligned
+      const cuuint64_t ds[3] = {(cuuint64_t)(D.nx & ~3), (cuuint64_t)D.ny, 72};
+      const cuuint32_t bs[3] = {32, 4, 72};
+      if (encode(ms, dt, 3, cell00, ds, strides, bs, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                 CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    }
+  return true;
+}
+
+// Forget the captured step graphs (they bake in the launch configuration).
+void drop_graphs(rlbm_ctx* h) {
+  for (int i = 0; i < 2; ++i) {
+    if (h->pair_graph[i]) cudaGraphExecDestroy(h->pair_graph[i]);
+    if (h->chunk_graph[i]) cudaGraphExecDestroy(h->chunk_graph[i]);
+    h->pair_graph[i] = h->chunk_graph[i] = nullptr;
+  }
 }
 
 // Staging area for host transfers: the population copy that does not hold the
@@ -232,6 +306,7 @@ int rlbm_create(const rlbm_config* c, rlbm_handle* out) {
   h->d_status = reinterpret_cast<unsigned*>(h->base + h->L.status_off);
   h->d_doms = reinterpret_cast<DomDev*>(h->base + h->L.doms_off);
   h->d_tiles = reinterpret_cast<Tile*>(h->base + h->L.tiles_off);
+  if (h->storage != RLBM_F64) h->d_tmaps = reinterpret_cast<unsigned char*>(h->base + h->L.tmaps_off);
   h->pop[0] = h->base + h->L.pop_off[0];
   h->pop[1] = h->base + h->L.pop_off[1];
   h->initialized.assign(h->ndom, 0);
@@ -251,6 +326,10 @@ int rlbm_create(const rlbm_config* c, rlbm_handle* out) {
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->d_tiles, h->L.tiles.data(), sizeof(Tile) * h->L.tiles.size(),
                         cudaMemcpyHostToDevice, h->stream);
+  std::vector<unsigned char> maps;
+  if (e == cudaSuccess && h->d_tmaps && !encode_tmaps(h, maps)) h->d_tmaps = nullptr;
+  if (e == cudaSuccess && h->d_tmaps)
+    e = cudaMemcpyAsync(h->d_tmaps, maps.data(), maps.size(), cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = launch_prepare_refs(h->edf, h->d_doms, h->ndom, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -466,36 +545,51 @@ int rlbm_tune(rlbm_handle h, int repeats) {
   cudaEvent_t t0, t1;
   if (cudaEventCreate(&t0) != cudaSuccess) return RLBM_E_CUDA;
   if (cudaEventCreate(&t1) != cudaSuccess) { cudaEventDestroy(t0); return RLBM_E_CUDA; }
+  // kernel variants: the mixed storages with TMA descriptors have two
+  std::vector<int> kernels = {RLBM_KERNEL_L1};
+  if (h->d_tmaps) kernels.push_back(RLBM_KERNEL_TMA);
   float best = 1e30f;
-  int best_grid = ntiles;
-  for (int g : cand) {
-    h->grid = g;
-    e = launch_step(h, h->cur);  // reads the current copy, writes the spare one
-    if (e == cudaSuccess) e = cudaEventRecord(t0, h->stream);
-    for (int r = 0; r < repeats && e == cudaSuccess; ++r) e = launch_step(h, h->cur);
-    if (e == cudaSuccess) e = cudaEventRecord(t1, h->stream);
-    if (e == cudaSuccess) e = cudaEventSynchronize(t1);
-    float ms = 0.0f;
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
-    if (e != cudaSuccess) break;
-    if (ms < best) {
-      best = ms;
-      best_grid = g;
+  int best_grid = ntiles, best_kernel = h->kernel;
+  for (int kv : kernels)
+    for (int g : cand) {
+      h->kernel = kv;
+      h->grid = g;
+      e = launch_step(h, h->cur);  // reads the current copy, writes the spare one
+      if (e == cudaSuccess) e = cudaEventRecord(t0, h->stream);
+      for (int r = 0; r < repeats && e == cudaSuccess; ++r) e = launch_step(h, h->cur);
+      if (e == cudaSuccess) e = cudaEventRecord(t1, h->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+      float ms = 0.0f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+      if (e != cudaSuccess) break;
+      if (ms < best) {
+        best = ms;
+        best_grid = g;
+        best_kernel = kv;
+      }
     }
-  }
   cudaEventDestroy(t0);
   cudaEventDestroy(t1);
   h->grid = best_grid;
-  for (int i = 0; i < 2; ++i) {
-    if (h->pair_graph[i]) cudaGraphExecDestroy(h->pair_graph[i]);
-    if (h->chunk_graph[i]) cudaGraphExecDestroy(h->chunk_graph[i]);
-    h->pair_graph[i] = h->chunk_graph[i] = nullptr;
-  }
+  h->kernel = best_kernel;
+  drop_graphs(h);
   *h->h_status = saved;
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->d_status, h->h_status, sizeof(unsigned), cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   return e == cudaSuccess ? best_grid : RLBM_E_CUDA;
+}
+
+int rlbm_select_kernel(rlbm_handle h, int kernel) {
+  if (!h) return RLBM_E_ARG;
+  if (kernel < 0) return h->kernel;
+  if (kernel != RLBM_KERNEL_L1 && kernel != RLBM_KERNEL_TMA) return RLBM_E_ARG;
+  if (kernel == RLBM_KERNEL_TMA && !h->d_tmaps) return RLBM_E_UNSUPPORTED;
+  if (kernel != h->kernel) {
+    h->kernel = kernel;
+    drop_graphs(h);
+  }
+  return kernel;
 }
 
 int rlbm_sync_status(rlbm_handle h) {
@@ -532,6 +626,7 @@ const char* rlbm_status_string(int code) {
     default: break;
   }
   if (code > 0) {
+    if (code & RLBM_W_DEVICE_TIMEOUT) return "error: a bounded device wait timed out (step results invalid)";
     if (code & RLBM_W_NONPHYSICAL) return "warning: non-physical state in some cell (left unrelaxed)";
     if (code & RLBM_W_ZSOLVE) return "warning: fugacity solve did not converge in some cell";
     if (code & RLBM_W_LANDAU_MAXITER) return "warning: Landau solve hit its iteration cap";

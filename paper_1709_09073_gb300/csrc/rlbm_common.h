@@ -10,7 +10,7 @@ enum { BC_PERIODIC = 0, BC_ZERO_GRADIENT = 1, BC_WALL = 2, BC_VWALL = 3 };
 enum { ST_F64 = 0, ST_F32 = 1, ST_BF16DEV = 2, ST_F16DEV = 3, ST_F32DEV = 4 };
 
 // per-cell status bits (identical to the public RLBM_W_* values)
-enum { ST_LANDAU = 1, ST_CLAMPED = 2, ST_NONPHYSICAL = 4, ST_ZSOLVE = 8 };
+enum { ST_LANDAU = 1, ST_CLAMPED = 2, ST_NONPHYSICAL = 4, ST_ZSOLVE = 8, ST_TIMEOUT = 16 };
 
 constexpr double PI = 3.14159265358979323846264338327950288;
 constexpr double ZC = 1.0 - 1.0e-7;  // BE reference fugacity, Eq. (15)
@@ -57,6 +57,18 @@ struct StepArgs {
   const void* fin;        // population copy read (post-collision, with halo)
   void* fout;             // population copy written
   unsigned* status;       // OR of per-cell status bits
+  const void* tmaps;      // TMA load descriptors of fin, one per domain (kTensorMapBytes each), or null
+  const void* tmaps_out;  // TMA store descriptors of fout (FP32 storages), or null
 };
+
+constexpr int kTensorMapBytes = 128;  // sizeof(CUtensorMap), 64-byte aligned in memory
+
+// TMA box of the staged mixed step: the six shell planes of one direction over a
+// 32 x 4 tile and its one-cell ring, rows y0-1 .. y0+4, columns from the 16-byte
+// boundary lpad elements left of x0 to at least x0+32 (a 16-byte multiple wide).
+constexpr int kBoxRows = 6;
+__host__ __device__ constexpr int tma_box_width(int esize) {
+  return (16 / esize + 33 + 16 / esize - 1) / (16 / esize) * (16 / esize);
+}
 
 }  // namespace rlbm

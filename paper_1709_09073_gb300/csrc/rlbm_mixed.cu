@@ -16,6 +16,7 @@
 
 #include "rlbm_dfloat.cuh"
 #include "rlbm_kernels.cuh"
+#include "rlbm_tma.cuh"
 
 namespace rlbm {
 
@@ -365,12 +366,14 @@ __device__ void write_halo_mixed(const DomDev& D, int x, int y, typename S::T* _
 // Collision of one cell (Eqs. 20-25, 10-11 and 3) from its pulled FP32
 // deviations, held in the thread's shared-memory column smf[q * kThreads + tid],
 // and the shell sums A_d = sum_s p_s dv_{6d+s}, B_d = sum_s p_s^2 dv_{6d+s} of
-// each direction; stores f* to fout, writes the cell's halo images and returns
-// its status bits.
-template <int EDF, class S>
+// each direction; stores f* to fout (kCol: encoded into the column instead,
+// FP32 storages only, for a bulk store of the tile), writes the cell's halo
+// images and returns its status bits.
+template <int EDF, class S, bool kCol = false>
 __device__ __forceinline__ unsigned collide_mixed(const DomDev& D, int x, int y, long long c, const float A[12],
                                                   const float B[12], float* smf, int tid,
                                                   typename S::T* __restrict__ fout) {
+  static_assert(!kCol || sizeof(typename S::T) == sizeof(float), "column output needs FP32 storage");
   const long long P = D.plane;
   const HarmF ha = harmonics_f(A), hb = harmonics_f(B);
   // moment totals in double-float: reference moments + FP32 deviation sums
@@ -457,14 +460,21 @@ __device__ __forceinline__ unsigned collide_mixed(const DomDev& D, int x, int y,
         const int q = 6 * d + s;
         const float v = smf[q * kThreads + tid];
         const float r = fmaf(om[d], fe[d] - v, v);
-        smf[q * kThreads + tid] = r;
-        fout[q * P + c] = S::encf(r, D, s);
+        if constexpr (kCol) {
+          smf[q * kThreads + tid] = S::encf(r, D, s);
+        } else {
+          smf[q * kThreads + tid] = r;
+          fout[q * P + c] = S::encf(r, D, s);
+        }
       }
     }
   } else {
-    for (int q = 0; q < 72; ++q) fout[q * P + c] = S::encf(smf[q * kThreads + tid], D, q % 6);
+    for (int q = 0; q < 72; ++q) {
+      if constexpr (kCol) smf[q * kThreads + tid] = S::encf(smf[q * kThreads + tid], D, q % 6);
+      else fout[q * P + c] = S::encf(smf[q * kThreads + tid], D, q % 6);
+    }
   }
-  write_halo_mixed<EDF, S>(D, x, y, fout, smf + tid, ok, nf, uxf, uyf, gf, st);
+  write_halo_mixed<EDF, S, !kCol>(D, x, y, fout, smf + tid, ok, nf, uxf, uyf, gf, st);
   return st;
 }
 
@@ -507,6 +517,182 @@ __global__ void __launch_bounds__(kThreads, RLBM_MIXED_MIN_BLOCKS) k_step_mixed(
 #undef RLBM_PULL_DIR
     const unsigned st = collide_mixed<EDF, S>(D, x, y, c, A, B, smf, tid, fout);
     if (st) atomicOr(a.status, st);
+  }
+}
+
+// ------------------------------------------- TMA-staged variant of the step
+// Per 32 x 4 tile and direction d, one TMA box brings the six shell planes of d
+// (rows y0-1 .. y0+4, columns from the 16-byte boundary left of x0-1 to past
+// x0+32) into shared memory; the bilinear pull reads its four neighbours there
+// at fixed offsets. A ring of kStages boxes keeps the next directions -- and,
+// while a tile collides, the next tile's first directions -- in flight. For FP32
+// storages the collided tile is encoded into the shared-memory column and
+// written back by one bulk tensor store over x < nx & ~3 (the store clips at the
+// tensor bounds, along x in 16-byte units, so the last nx % 4 cells of a row
+// store their own values). The arithmetic is the same as k_step_mixed's, so the
+// two variants give identical results.
+template <class S>
+struct TmaBox {
+  using T = typename S::T;
+  static constexpr int kLpad = 16 / (int)sizeof(T);         // elements left of x = 0 in a row
+  static constexpr int kW = tma_box_width((int)sizeof(T));  // 40 (FP32) or 48 (16-bit) elements
+  static constexpr int kRows = kBoxRows;                      // y0-1 .. y0+4
+  static constexpr int kPlaneElems = kW * kRows;
+  static constexpr unsigned kBytes = (unsigned)(kPlaneElems * 6 * sizeof(T));  // six shells
+  static constexpr int kStageElems = (int)(kBytes / sizeof(T));
+};
+constexpr int kStages = 3;  // ring depth in directions (a divisor of 12)
+
+template <class S>
+constexpr size_t tma_smem_bytes() {
+  return kStages * (size_t)TmaBox<S>::kBytes + 72 * kThreads * sizeof(float) + kStages * sizeof(uint64_t);
+}
+
+// Issue the box of direction d of tile t into its ring stage (one thread).
+template <class S>
+__device__ __forceinline__ void tma_issue(const StepArgs& a, int t, int d, unsigned char* ring, uint64_t* bar) {
+  const Tile tl = a.tiles[t];
+  const void* map = static_cast<const unsigned char*>(a.tmaps) + (size_t)tl.dom * kTensorMapBytes;
+  const int k = d % kStages;
+  mbar_expect_tx(&bar[k], TmaBox<S>::kBytes);
+  tma_load_3d(ring + k * TmaBox<S>::kBytes, map, tl.x0, tl.y0, 6 * d, &bar[k]);
+}
+
+// Pull of direction d from its staged box; `cell` points at the cell's own
+// value in shell 0 of that stage (same weights and order of operations as
+// pull_one), col at the thread's shared-memory column.
+template <int d, class S>
+__device__ __forceinline__ void pull_dir_staged(const typename S::T* cell, const DomDev& D, const float pc[6],
+                                                const float p2c[6], float* col, float& A, float& B) {
+  using TB = TmaBox<S>;
+  constexpr double cx = dcos(d), cy = dsin(d);
+  constexpr int sx = sgnd(cx), sy = sgnd(cy);
+  constexpr double ax = dabs(cx), ay = dabs(cy);
+  constexpr float axr = (float)ax, ayr = (float)ay;
+  constexpr float w1 = axr * ayr, w2 = (1.0f - axr) * ayr, w3 = axr * (1.0f - ayr),
+                  w4 = (1.0f - axr) * (1.0f - ayr);
+  constexpr int o1 = -sx - sy * TB::kW, o2 = -sy * TB::kW, o3 = -sx;
+  float a_ = 0.0f, b_ = 0.0f;
+#pragma unroll
+  for (int s = 0; s < 6; ++s) {
+    const typename S::T* pl = cell + s * TB::kPlaneElems;
+    float v;
+    if (ax == 0.0 || ay == 0.0) {
+      v = S::raw(pl[o1]);
+    } else {
+      const float v1 = S::raw(pl[o1]), v2 = S::raw(pl[o2]), v3 = S::raw(pl[o3]), v4 = S::raw(pl[0]);
+      v = fmaf(w1, v1, fmaf(w2, v2, fmaf(w3, v3, w4 * v4)));
+    }
+    v = S::decf(v, D, s);
+    col[(6 * d + s) * kThreads] = v;
+    a_ = fmaf(v, pc[s], a_);
+    b_ = fmaf(v, p2c[s], b_);
+  }
+  A = a_;
+  B = b_;
+}
+
+template <int EDF, class S>
+__global__ void __launch_bounds__(kThreads, RLBM_MIXED_MIN_BLOCKS) k_step_mixed_tma(StepArgs a) {
+  using T = typename S::T;
+  using TB = TmaBox<S>;
+  constexpr bool kCol = sizeof(T) == sizeof(float);  // bulk store of the collided tile
+  extern __shared__ __align__(128) unsigned char smt[];
+  unsigned char* ring = smt;
+  float* smf = reinterpret_cast<float*>(smt + kStages * TB::kBytes);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smt + kStages * TB::kBytes + 72 * kThreads * sizeof(float));
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  if (blockIdx.x >= a.ntiles) return;  // whole block
+  if (tid == 0) {
+#pragma unroll
+    for (int k = 0; k < kStages; ++k) mbar_init(&bar[k], 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  // thread 0 tracks the loads in flight per stage (for the drain on a timeout)
+  unsigned inflight = 0, issued[kStages] = {};
+  if (tid == 0) {
+#pragma unroll
+    for (int d = 0; d < kStages; ++d) {
+      tma_issue<S>(a, blockIdx.x, d, ring, bar);
+      inflight |= 1u << d;
+      ++issued[d];
+    }
+  }
+  // the cell's own value in shell 0 of stage 0, and its column
+  const T* cell0 = reinterpret_cast<const T*>(ring) + (threadIdx.y + 1) * TB::kW + threadIdx.x + TB::kLpad;
+  float* col = smf + tid;
+  float pc[6], p2c[6];
+#pragma unroll
+  for (int s = 0; s < 6; ++s) {
+    pc[s] = c_pf[EDF][s];
+    p2c[s] = c_p2f[EDF][s];
+  }
+  unsigned it = 0;  // tiles done by this block: stage uses so far = it * 12 / kStages + d / kStages
+  for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++it) {
+    const Tile tl = a.tiles[t];
+    const DomDev& D = a.doms[tl.dom];
+    const int x = tl.x0 + threadIdx.x, y = tl.y0 + threadIdx.y;
+    const int tnext = t + gridDim.x;
+    const unsigned use0 = it * (12 / kStages);
+    if (kCol && t != (int)blockIdx.x) {  // the previous tile's bulk store has read the column
+      if (tid == 0) bulk_wait_read();
+      __syncthreads();
+    }
+    float A[12], B[12];
+    // every lane pulls (lanes outside the domain read the box's padding and
+    // fill only their own column, which is never stored)
+#define RLBM_STAGED_DIR(d)                                                                      \
+  {                                                                                             \
+    constexpr int k_ = (d) % kStages;                                                           \
+    const bool ok_ = mbar_wait(&bar[k_], (use0 + (d) / kStages) & 1);                           \
+    pull_dir_staged<d, S>(cell0 + k_ * TB::kStageElems, D, pc, p2c, col, A[d], B[d]);           \
+    if (__syncthreads_or(!ok_)) goto timed_out;                                                 \
+    if (tid == 0) {                                                                             \
+      inflight &= ~(1u << k_);                                                                  \
+      const int tt_ = (d) + kStages < 12 ? t : tnext;                                           \
+      if (tt_ < a.ntiles) {                                                                     \
+        tma_issue<S>(a, tt_, ((d) + kStages) % 12, ring, bar);                                  \
+        inflight |= 1u << k_;                                                                   \
+        ++issued[k_];                                                                           \
+      }                                                                                         \
+    }                                                                                           \
+  }
+    RLBM_STAGED_DIR(0) RLBM_STAGED_DIR(1) RLBM_STAGED_DIR(2) RLBM_STAGED_DIR(3)
+    RLBM_STAGED_DIR(4) RLBM_STAGED_DIR(5) RLBM_STAGED_DIR(6) RLBM_STAGED_DIR(7)
+    RLBM_STAGED_DIR(8) RLBM_STAGED_DIR(9) RLBM_STAGED_DIR(10) RLBM_STAGED_DIR(11)
+#undef RLBM_STAGED_DIR
+    if (x < D.nx && y < D.ny) {
+      T* __restrict__ fout = static_cast<T*>(a.fout) + D.off;
+      const long long c = (long long)(y + 1) * D.pitch + D.lpad + x;
+      const unsigned st = collide_mixed<EDF, S, kCol>(D, x, y, c, A, B, smf, tid, fout);
+      if (st) atomicOr(a.status, st);
+      if constexpr (kCol) {  // the bulk store covers x < nx & ~3 (16-byte clipping)
+        if (x >= (D.nx & ~3))
+          for (int q = 0; q < 72; ++q) fout[q * D.plane + c] = col[q * kThreads];
+      }
+    }
+    if constexpr (kCol) {
+      fence_async_smem();
+      __syncthreads();
+      if (tid == 0) {
+        const void* smap = static_cast<const unsigned char*>(a.tmaps_out) + (size_t)tl.dom * kTensorMapBytes;
+        tma_store_3d(smap, smf, tl.x0, tl.y0, 0);
+        bulk_commit();
+      }
+    }
+  }
+  if (kCol && tid == 0) bulk_wait_all();
+  return;
+timed_out:
+  // a copy did not land in time: report it, let the copies still in flight
+  // finish (bounded) so that none writes shared memory after exit, return
+  if (tid == 0) {
+    atomicOr(a.status, ST_TIMEOUT);
+    if (kCol) bulk_wait_all();
+#pragma unroll
+    for (int k = 0; k < kStages; ++k)
+      if (inflight & (1u << k)) mbar_wait(&bar[k], (issued[k] - 1) & 1);
   }
 }
 
@@ -567,9 +753,21 @@ static const double h_g_zc[6] = RLBM_G_ZC_INIT;
 
 constexpr size_t kSmemF = 72 * kThreads * sizeof(float);
 
+template <class S, int EDF>
+static cudaError_t prepare_tma_t() {
+  cudaError_t e = cudaFuncSetAttribute(k_step_mixed_tma<EDF, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)tma_smem_bytes<S>());
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_step_mixed_tma<EDF, S>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                              (int)cudaSharedmemCarveoutMaxShared);
+}
+
 template <class S>
 static cudaError_t prepare_s() {
   cudaError_t e;
+  if ((e = prepare_tma_t<S, EDF_MJ>())) return e;
+  if ((e = prepare_tma_t<S, EDF_FD>())) return e;
+  if ((e = prepare_tma_t<S, EDF_BE>())) return e;
   if ((e = prepare_common_t<S, EDF_MJ>())) return e;
   if ((e = prepare_common_t<S, EDF_FD>())) return e;
   return prepare_common_t<S, EDF_BE>();
@@ -617,6 +815,15 @@ cudaError_t launch_prepare_refs(int edf, DomDev* doms, int ndom, cudaStream_t s)
 
 template <class S>
 static cudaError_t step_s(int edf, const StepArgs& a, int grid, cudaStream_t s) {
+  if (a.tmaps) {  // TMA-staged variant; without descriptors the pull goes through L1
+    const size_t sm = tma_smem_bytes<S>();
+    switch (edf) {
+      case EDF_MJ: k_step_mixed_tma<EDF_MJ, S><<<grid, dim3(32, 4), sm, s>>>(a); break;
+      case EDF_FD: k_step_mixed_tma<EDF_FD, S><<<grid, dim3(32, 4), sm, s>>>(a); break;
+      default: k_step_mixed_tma<EDF_BE, S><<<grid, dim3(32, 4), sm, s>>>(a); break;
+    }
+    return cudaGetLastError();
+  }
   switch (edf) {
     case EDF_MJ: k_step_mixed<EDF_MJ, S><<<grid, dim3(32, 4), kSmemF, s>>>(a); break;
     case EDF_FD: k_step_mixed<EDF_FD, S><<<grid, dim3(32, 4), kSmemF, s>>>(a); break;

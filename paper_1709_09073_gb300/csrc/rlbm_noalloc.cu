@@ -183,6 +183,8 @@ extern "C" int rlbm_step_noalloc(const rlbm_domain* domain, int edf, int nsteps,
     a.fin = pop[cur];
     a.fout = pop[1 - cur];
     a.status = d_status;
+    a.tmaps = nullptr;
+    a.tmaps_out = nullptr;
     e = launch_step_f64(edf, a, P.ntiles, s);
     cur = 1 - cur;
   }

@@ -22,11 +22,14 @@ RLBM_OK = 0
 RLBM_W_LANDAU_MAXITER, RLBM_W_CLAMPED_FUGACITY, RLBM_W_NONPHYSICAL, RLBM_W_ZSOLVE = 1, 2, 4, 8
 RLBM_E_ARG, RLBM_E_CUDA, RLBM_E_STATE, RLBM_E_UNSUPPORTED, RLBM_E_NOBUFFER = -1, -2, -3, -4, -5
 RLBM_E_SCRATCH = -6
+RLBM_W_DEVICE_TIMEOUT = 16
+RLBM_KERNEL_L1, RLBM_KERNEL_TMA = 0, 1
 RLBM_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 EXPORTS = ["rlbm_workspace_bytes", "rlbm_create", "rlbm_init", "rlbm_step", "rlbm_moments",
            "rlbm_get_populations", "rlbm_set_populations", "rlbm_tune", "rlbm_sync_status",
-           "rlbm_destroy", "rlbm_status_string", "rlbm_last_step_info", "rlbm_step_noalloc", "rlbm_diagnostics"]
+           "rlbm_destroy", "rlbm_status_string", "rlbm_last_step_info", "rlbm_step_noalloc", "rlbm_diagnostics",
+           "rlbm_select_kernel"]
 
 
 class rlbm_domain(ctypes.Structure):
@@ -72,6 +75,7 @@ def load(path=None):
     L.rlbm_get_populations.argtypes = [_H, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]
     L.rlbm_set_populations.argtypes = [_H, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]
     L.rlbm_tune.argtypes = [_H, ctypes.c_int]
+    L.rlbm_select_kernel.argtypes = [_H, ctypes.c_int]
     L.rlbm_diagnostics.argtypes = [_H, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]
     L.rlbm_sync_status.argtypes = [_H]
     L.rlbm_destroy.argtypes = [_H]
@@ -193,6 +197,11 @@ class Simulation:
     def tune(self, repeats=3):
         """Autotune the step launch (grid shape) on the current state; returns the grid."""
         return _check(load().rlbm_tune(self.h, repeats))
+
+    def select_kernel(self, kernel=-1):
+        """Select the mixed step variant (RLBM_KERNEL_L1 / RLBM_KERNEL_TMA) or,
+        with no argument, return the one in use."""
+        return _check(load().rlbm_select_kernel(self.h, kernel))
 
     def sync_status(self):
         return _check(load().rlbm_sync_status(self.h))

@@ -1,0 +1,79 @@
+"""The TMA-staged variant of the mixed step (RLBM_KERNEL_TMA) against the L1
+variant: the same arithmetic, so the populations (halo ring included) must be
+bit-identical, for every mixed storage and EDF, on ragged walled domains
+(widths not multiples of 4 exercise the bulk store's tail) and on a batch of
+uneven domains under the persistent grid the tuner may pick."""
+import numpy as np
+import pytest
+
+from paper_1709_09073_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+STORAGES = {"f32": 1, "f32dev": 4, "f16dev": 3, "bf16dev": 2}
+
+
+@pytest.fixture(scope="module")
+def R():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_1709_09073_gb300 import build, rlbm
+    build.build()
+    rlbm.load()
+    return rlbm
+
+
+def _populations(R, specs, inits, storage, kernel, steps, grid_tune=False):
+    sim = R.Simulation(specs, edf=specs[0].edf, storage=storage)
+    for i, s in enumerate(inits):
+        sim.init(i, s)
+    if grid_tune:
+        sim.tune(1)
+    assert sim.select_kernel(kernel) == kernel
+    sim.step(steps)
+    st = sim.sync_status()
+    out = [sim.get_populations(i) for i in range(len(specs))]
+    sim.close()
+    return out, st
+
+
+@pytest.mark.parametrize("edf", [0, 1, 2])
+@pytest.mark.parametrize("stname", list(STORAGES))
+def test_tma_matches_l1_bitwise(R, edf, stname):
+    spec = W.DomainSpec(37, 11, 0.8, edf, (W.FIXED_T_WALL, W.FIXED_T_WALL, W.PERIODIC, W.PERIODIC),
+                        (0.97, 1.03, 1.0, 1.0))
+    init = W.random_domain_state(37, 11, 50 + edf, edf, u_amp=0.05)
+    a, sa = _populations(R, [spec], [init], STORAGES[stname], R.RLBM_KERNEL_L1, 12)
+    b, sb = _populations(R, [spec], [init], STORAGES[stname], R.RLBM_KERNEL_TMA, 12)
+    assert sa == sb and (sa & R.RLBM_W_DEVICE_TIMEOUT) == 0
+    assert np.array_equal(a[0], b[0])
+
+
+def test_tma_matches_l1_on_a_tuned_batch(R):
+    specs = [W.DomainSpec(33, 17, 0.7, 0), W.DomainSpec(64, 8, 1.3, 0, (1, 1, 0, 0)),
+             W.DomainSpec(101, 40, 0.9, 0, (2, 2, 0, 0), (0.95, 1.05, 1, 1)),
+             W.DomainSpec(6, 7, 1.1, 0), W.DomainSpec(130, 3, 2.0, 0, (0, 0, 1, 1))]
+    inits = [W.random_domain_state(s.nx, s.ny, 40 + i) for i, s in enumerate(specs)]
+    a, _ = _populations(R, specs, inits, 4, R.RLBM_KERNEL_L1, 9, grid_tune=True)
+    b, st = _populations(R, specs, inits, 4, R.RLBM_KERNEL_TMA, 9, grid_tune=True)
+    assert st == 0
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+def test_kernel_selection_rules(R):
+    sim = R.Simulation([W.DomainSpec(16, 8, 0.9, 0)], storage=R.RLBM_F64)
+    assert sim.select_kernel() == R.RLBM_KERNEL_L1
+    with pytest.raises(R.RlbmError):
+        sim.select_kernel(R.RLBM_KERNEL_TMA)  # FP64 storage has no staged variant
+    sim.close()
+    narrow = R.Simulation([W.DomainSpec(3, 8, 0.9, 0)], storage=R.RLBM_F32DEV)
+    with pytest.raises(R.RlbmError):
+        narrow.select_kernel(R.RLBM_KERNEL_TMA)  # narrower than 4 cells: no descriptors
+    with pytest.raises(R.RlbmError):
+        narrow.select_kernel(7)
+    narrow.close()
+    sim = R.Simulation([W.DomainSpec(64, 16, 0.9, 0)], storage=R.RLBM_F32DEV)
+    sim.init(0, W.random_domain_state(64, 16, 1))
+    assert sim.tune(1) > 0 and sim.select_kernel() in (R.RLBM_KERNEL_L1, R.RLBM_KERNEL_TMA)
+    sim.close()
