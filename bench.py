@@ -298,11 +298,11 @@ def run_native(args):
 
 
 # FP64 operations per cell update of the plain kernel (k_step_f64<MJ>), FMA = 2:
-# 830 DFMA + 308 DADD + 202 DMUL per cell, the executed-instruction counts ncu
+# 872 DFMA + 308 DADD + 202 DMUL per cell, the executed-instruction counts ncu
 # reports for one 1024^2 launch divided by its cells; used for the FP64 ALU
 # roofline of the plain form.
-FP64_FLOPS_PER_CELL = 2 * 830 + 308 + 202
-FP64_INSTR_PER_CELL = 830 + 308 + 202
+FP64_FLOPS_PER_CELL = 2 * 872 + 308 + 202
+FP64_INSTR_PER_CELL = 872 + 308 + 202
 
 
 def cpu_baseline(wl, budget_s=15.0):
@@ -337,10 +337,13 @@ def run_profile_case(args):
     L, storage = (2048, rlbm.RLBM_F32DEV) if args.profile_case == "mixed" else (1024, rlbm.RLBM_F64)
     wl = W.taylor_green(L=L, u0=0.02, tau=0.9, steps=3)
     sim, _ = rlbm.from_workload(wl, storage=storage)
+    if args.kernel != "l1":
+        sim.select_kernel(rlbm.RLBM_KERNEL_TMA)
     sim.step(3)
     torch.cuda.synchronize()
     t = timed_steps(sim, args.steps, torch) if args.steps > 0 else 0.0
-    print(json.dumps({"profile_case": args.profile_case, "cells": wl.cells, "status": sim.sync_status(),
+    print(json.dumps({"profile_case": args.profile_case, "kernel": args.kernel, "cells": wl.cells,
+                      "status": sim.sync_status(),
                       "steps": args.steps, "mlups": round(wl.cells * args.steps / t / 1e6, 1) if t else None}))
 
 
@@ -434,6 +437,8 @@ def main():
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the hot-spot and Fourier-flow configurations")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--kernel", choices=["l1", "tma"], default="l1",
+                    help="mixed step variant of --profile-case mixed")
     ap.add_argument("--profile-case", choices=["mixed", "fp64"], default=None,
                     help="run a small single-domain case for ncu instead of the benchmark")
     args = ap.parse_args()

@@ -30,8 +30,12 @@ __global__ void __launch_bounds__(kThreads) k_step_f64(StepArgs a) {
     if (ok) {
       // constant tau, or the local tau = 4 (eta/s) / theta + 0.2546 of Sec. 3.5;
       // a body force shifts the velocity the collision uses to u + a tau (Sec. 3.4)
-      const double tau = D.eta_s > 0.0 ? 4.0 * D.eta_s / S.theta + 0.2546 : D.tau;
-      const double itau = D.eta_s > 0.0 ? 1.0 / tau : D.inv_tau;
+      // (a branch, uniform per domain: the divisions only run for a local tau)
+      double tau = D.tau, itau = D.inv_tau;
+      if (D.eta_s > 0.0) {
+        tau = 4.0 * D.eta_s / S.theta + 0.2546;
+        itau = 1.0 / tau;
+      }
       double ux = S.ux, uy = S.uy, gam = S.gamma;
       if (D.accel_x != 0.0 || D.accel_y != 0.0) {
         ux += D.accel_x * tau;

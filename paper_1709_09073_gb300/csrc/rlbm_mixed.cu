@@ -447,7 +447,8 @@ __device__ __forceinline__ unsigned collide_mixed(const DomDev& D, int x, int y,
     zr[4] -= d21r;
     zi[4] -= d21i;
     // constant tau, or the local tau = 4 (eta/s) / theta + 0.2546 of Sec. 3.5
-    const float itau = D.eta_s > 0.0 ? 1.0f / (4.0f * (float)D.eta_s / theta + 0.2546f) : (float)D.inv_tau;
+    float itau = (float)D.inv_tau;
+    if (D.eta_s > 0.0) itau = 1.0f / (4.0f * (float)D.eta_s / theta + 0.2546f);
     float om[12];
 #pragma unroll
     for (int d = 0; d < 12; ++d) om[d] = gf * (1.0f - ((float)dcos(d) * uxf + (float)dsin(d) * uyf)) * itau;
