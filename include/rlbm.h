@@ -165,6 +165,41 @@ int rlbm_diagnostics(rlbm_handle h, int domain, int streamed, double *out, int o
 int rlbm_get_populations(rlbm_handle h, int domain, double *f, int on_device);
 int rlbm_set_populations(rlbm_handle h, int domain, const double *f, int on_device);
 
+/* ---- y-slab halo rows ----------------------------------------------------
+ * One domain too large for one GPU is cut into y-slabs, one handle (or one
+ * domain of a handle) each, whose y sides that border another slab are given
+ * RLBM_ZERO_GRADIENT. The pull of the interpolated streaming (Eqs. 17-18)
+ * reaches one row: row 0 reads the ghost row y = -1 only in the 30 planes
+ * q = 6..35 (directions d = 1..5, v_y > 0) and row ny-1 reads y = ny only in
+ * q = 42..71 (d = 7..11, v_y < 0). Before every rlbm_step (and after
+ * rlbm_init) each slab therefore packs its two edge rows, sends them to its y
+ * neighbours (NCCL, a peer copy, or a plain device copy for slabs on one GPU)
+ * and unpacks what it receives into its ghost rows. Slabs stepped this way
+ * reproduce the undivided domain bit for bit.
+ *
+ * A packed face is [30][nx + 2] elements of the handle's storage type in its
+ * storage encoding (index k*(nx + 2) + x + 1 for x in -1..nx, plane 6 + k or
+ * 42 + k), so slabs that exchange rows must share nx, storage, ref_n,
+ * ref_theta and scale. rlbm_edge_row_bytes gives its size (0 for bad
+ * arguments). */
+size_t rlbm_edge_row_bytes(rlbm_handle h, int domain);
+
+/* Pack the current post-collision edge rows of `domain` into device buffers:
+ * `lo` <- row 0, planes 42..71 (what the slab below reads), `hi` <- row ny-1,
+ * planes 6..35 (what the slab above reads), each with its two x ghost values.
+ * Either pointer may be NULL (that face is skipped); non-NULL ones are device
+ * memory of rlbm_edge_row_bytes() bytes, aligned to the element size. Runs on
+ * the handle's stream (one kernel launch), asynchronously. RLBM_E_STATE for an
+ * uninitialised domain. */
+int rlbm_pack_edge_rows(rlbm_handle h, int domain, void *lo, void *hi);
+
+/* Write received edge rows into the ghost rows of `domain`: `lo` (the top row
+ * of the slab below, planes 6..35) into y = -1, `hi` (the bottom row of the
+ * slab above, planes 42..71) into y = ny. The other planes of the ghost rows
+ * are left as they are. Pointers, sizes and errors as for
+ * rlbm_pack_edge_rows; asynchronous on the handle's stream. */
+int rlbm_unpack_ghost_rows(rlbm_handle h, int domain, const void *lo, const void *hi);
+
 /* Autotune the launch of the step kernel on the current state (left unchanged):
  * time `repeats` launches of each candidate -- every kernel variant the handle
  * has (rlbm_select_kernel) with one block per 32 x 4 tile or a persistent grid

@@ -273,6 +273,69 @@ void drop_graphs(rlbm_ctx* h) {
 double* staging(rlbm_ctx* h) { return static_cast<double*>(h->pop[1 - h->cur]); }
 size_t staging_doubles(rlbm_ctx* h) { return h->L.pop_bytes / sizeof(double); }
 
+constexpr int kSlabPlanes = 30;  // 5 directions with v_y of one sign x 6 shells
+constexpr int kPlanesUp = 6;     // q = 6..35: d = 1..5, v_y > 0
+constexpr int kPlanesDown = 42;  // q = 42..71: d = 7..11, v_y < 0
+
+// Geometry of one domain's rows in a halo-padded population copy.
+struct RowArgs {
+  int nx, ny, pitch, lpad;
+  long long plane, off;
+  int unpack;       // 0: edge rows -> packed faces, 1: packed faces -> ghost rows
+  void* pop;
+  void* face[2];    // low, high; either may be null
+};
+
+// Raw element copy between a packed [30][nx + 2] face and one row of 30
+// planes, both faces in one launch (the storage encoding is kept as is).
+template <class T>
+__global__ void k_rows(RowArgs a) {
+  const long long w = a.nx + 2, per = kSlabPlanes * w;
+  T* pop = static_cast<T*>(a.pop);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < 2 * per;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int side = e >= per;
+    T* buf = static_cast<T*>(a.face[side]);
+    if (!buf) continue;
+    const long long r = e - side * per, k = r / w, xx = r % w;
+    // sent rows: row 0 down (planes 42..), row ny-1 up (planes 6..);
+    // received rows: y = -1 gets planes 6.., y = ny gets planes 42..
+    const int q0 = (side == 0) == (a.unpack != 0) ? kPlanesUp : kPlanesDown;
+    const int y = a.unpack ? (side ? a.ny : -1) : (side ? a.ny - 1 : 0);
+    const long long idx = a.off + (q0 + k) * a.plane + (long long)(y + 1) * a.pitch + (a.lpad - 1) + xx;
+    if (a.unpack) pop[idx] = buf[r];
+    else buf[r] = pop[idx];
+  }
+}
+
+int slab_rows(rlbm_handle h, int domain, void* lo, void* hi, int unpack) {
+  if (!h || domain < 0 || domain >= h->ndom) return RLBM_E_ARG;
+  if (!h->initialized[domain]) return RLBM_E_STATE;
+  const size_t es = h->L.esize;
+  if ((reinterpret_cast<uintptr_t>(lo) % es) || (reinterpret_cast<uintptr_t>(hi) % es)) return RLBM_E_ARG;
+  if (!lo && !hi) return RLBM_OK;
+  const DomDev& D = h->L.dd[domain];
+  RowArgs a;
+  a.nx = D.nx;
+  a.ny = D.ny;
+  a.pitch = D.pitch;
+  a.lpad = D.lpad;
+  a.plane = D.plane;
+  a.off = D.off;
+  a.unpack = unpack;
+  a.pop = h->pop[h->cur];
+  a.face[0] = lo;
+  a.face[1] = hi;
+  const long long n = 2LL * kSlabPlanes * (D.nx + 2);
+  const int grid = (int)std::min<long long>((n + 255) / 256, 1216);
+  switch (es) {
+    case 8: k_rows<unsigned long long><<<grid, 256, 0, h->stream>>>(a); break;
+    case 4: k_rows<unsigned><<<grid, 256, 0, h->stream>>>(a); break;
+    default: k_rows<unsigned short><<<grid, 256, 0, h->stream>>>(a); break;
+  }
+  return cuda_fail(cudaGetLastError());
+}
+
 }  // namespace
 
 extern "C" {
@@ -523,6 +586,19 @@ int rlbm_get_populations(rlbm_handle h, int domain, double* f, int on_device) {
 
 int rlbm_set_populations(rlbm_handle h, int domain, const double* f, int on_device) {
   return copy_pops(h, domain, const_cast<double*>(f), on_device, 0);
+}
+
+size_t rlbm_edge_row_bytes(rlbm_handle h, int domain) {
+  if (!h || domain < 0 || domain >= h->ndom) return 0;
+  return (size_t)kSlabPlanes * (size_t)(h->doms[domain].nx + 2) * h->L.esize;
+}
+
+int rlbm_pack_edge_rows(rlbm_handle h, int domain, void* lo, void* hi) {
+  return slab_rows(h, domain, lo, hi, 0);
+}
+
+int rlbm_unpack_ghost_rows(rlbm_handle h, int domain, const void* lo, const void* hi) {
+  return slab_rows(h, domain, const_cast<void*>(lo), const_cast<void*>(hi), 1);
 }
 
 int rlbm_tune(rlbm_handle h, int repeats) {

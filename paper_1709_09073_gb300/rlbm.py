@@ -29,7 +29,7 @@ RLBM_NOALLOC_SCRATCH_BYTES = 32 << 20
 EXPORTS = ["rlbm_workspace_bytes", "rlbm_create", "rlbm_init", "rlbm_step", "rlbm_moments",
            "rlbm_get_populations", "rlbm_set_populations", "rlbm_tune", "rlbm_sync_status",
            "rlbm_destroy", "rlbm_status_string", "rlbm_last_step_info", "rlbm_step_noalloc", "rlbm_diagnostics",
-           "rlbm_select_kernel"]
+           "rlbm_select_kernel", "rlbm_edge_row_bytes", "rlbm_pack_edge_rows", "rlbm_unpack_ghost_rows"]
 
 
 class rlbm_domain(ctypes.Structure):
@@ -82,6 +82,10 @@ def load(path=None):
     L.rlbm_status_string.argtypes = [ctypes.c_int]
     L.rlbm_status_string.restype = ctypes.c_char_p
     L.rlbm_last_step_info.argtypes = [_H, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_int)]
+    L.rlbm_edge_row_bytes.argtypes = [_H, ctypes.c_int]
+    L.rlbm_edge_row_bytes.restype = ctypes.c_size_t
+    L.rlbm_pack_edge_rows.argtypes = [_H, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    L.rlbm_unpack_ghost_rows.argtypes = [_H, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
     L.rlbm_step_noalloc.argtypes = [ctypes.POINTER(rlbm_domain), ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint)]
     _lib = L
@@ -193,6 +197,31 @@ class Simulation:
     def set_populations(self, domain, f):
         f = np.ascontiguousarray(f, dtype=np.float64)
         _check(load().rlbm_set_populations(self.h, domain, f.ctypes.data_as(ctypes.c_void_p), 0))
+
+    # y-slab halo rows: packed faces are [30][nx + 2] device tensors of the
+    # storage element type (raw storage encoding)
+    _ROW_DTYPE = {RLBM_F64: "float64", RLBM_F32: "float32", RLBM_F32DEV: "float32",
+                  RLBM_BF16DEV: "int16", RLBM_F16DEV: "int16"}
+
+    def edge_row_buffer(self, domain):
+        """An empty packed face for `domain` on the workspace's device."""
+        n = load().rlbm_edge_row_bytes(self.h, domain)
+        if n == 0:
+            raise RlbmError("bad domain %d" % domain)
+        dt = getattr(self.torch, self._ROW_DTYPE[self.storage])
+        return self.torch.empty((30, self.specs[domain].nx + 2), dtype=dt, device=self.workspace.device)
+
+    def pack_edge_rows(self, domain, lo, hi):
+        """Bottom row (planes 42..71) into `lo`, top row (planes 6..35) into
+        `hi`; either may be None. Asynchronous on the handle's stream."""
+        p = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
+        _check(load().rlbm_pack_edge_rows(self.h, domain, p(lo), p(hi)))
+
+    def unpack_ghost_rows(self, domain, lo, hi):
+        """Rows received from the slab below (`lo`) and above (`hi`) into the
+        ghost rows y = -1 and y = ny; either may be None."""
+        p = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
+        _check(load().rlbm_unpack_ghost_rows(self.h, domain, p(lo), p(hi)))
 
     def tune(self, repeats=3):
         """Autotune the step launch (grid shape) on the current state; returns the grid."""

@@ -11,8 +11,10 @@ that x walls and x periodicity need nothing more. Rows are [72][nx + 2]
 arrays; the planes a neighbour does not need are left NaN.
 
 The exchange below uses torch.distributed point-to-point messages (gloo on the
-host, NCCL between GPUs); the batched benchmark shards whole domains instead
-and needs none of this.
+host, NCCL between GPUs). On a GPU the rows never leave the device: librlbm
+packs a slab's two edge rows into [30][nx + 2] faces in the storage encoding
+and writes received faces into its ghost rows (DeviceSlab). The batched
+benchmark shards whole domains instead and needs none of this.
 """
 import numpy as np
 
@@ -90,26 +92,90 @@ class SlabExchange:
         self.below, self.above = neighbours(rank, nranks, periodic_y)
         self.up, self.down = planes_up(), planes_down()
 
-    def exchange(self, bottom_row, top_row):
-        """Send this slab's edge rows, receive the neighbours'; returns
-        (row_lo, row_hi), each None at a non-periodic end of the domain."""
-        import torch
+    def exchange_packed(self, send_lo, send_hi, recv_lo, recv_hi):
+        """Send the packed faces (send_lo: the bottom row's planes for the slab
+        below, send_hi: the top row's for the slab above) and receive the
+        neighbours' into recv_lo (from below) and recv_hi (from above). Torch
+        tensors on the process group's device (CPU for gloo, the rank's GPU
+        for NCCL); faces toward a non-periodic end of the domain are skipped.
+        Both sends are posted before both receives, rows travelling up first
+        on either side, so that two ranks that are each other's neighbour on
+        both faces match their messages in order as well as by tag. Device
+        faces over a host-only backend (gloo) are staged through host memory."""
         import torch.distributed as dist
-        reqs, recv_lo, recv_hi = [], None, None
-        shape = (len(self.up), self.nx + 2)
+        stage = send_lo.is_cuda and dist.get_backend() == "gloo"
+        if stage:
+            dev_lo, dev_hi = recv_lo, recv_hi
+            send_lo, send_hi = send_lo.cpu(), send_hi.cpu()
+            recv_lo, recv_hi = send_lo.new_empty(send_lo.shape), send_hi.new_empty(send_hi.shape)
+        ops = []
         if self.above is not None:
-            reqs.append(dist.isend(torch.from_numpy(pack(top_row, self.up)), self.above, tag=self.UP))
-            recv_hi = torch.empty(shape, dtype=torch.float64)
-            reqs.append(dist.irecv(recv_hi, self.above, tag=self.DOWN))
+            ops.append(dist.P2POp(dist.isend, send_hi, self.above, tag=self.UP))
         if self.below is not None:
-            reqs.append(dist.isend(torch.from_numpy(pack(bottom_row, self.down)), self.below, tag=self.DOWN))
-            recv_lo = torch.empty(shape, dtype=torch.float64)
-            reqs.append(dist.irecv(recv_lo, self.below, tag=self.UP))
-        for r in reqs:
-            r.wait()
-        row_lo = unpack(recv_lo.numpy(), self.up, self.nx) if recv_lo is not None else None
-        row_hi = unpack(recv_hi.numpy(), self.down, self.nx) if recv_hi is not None else None
+            ops.append(dist.P2POp(dist.isend, send_lo, self.below, tag=self.DOWN))
+            ops.append(dist.P2POp(dist.irecv, recv_lo, self.below, tag=self.UP))
+        if self.above is not None:
+            ops.append(dist.P2POp(dist.irecv, recv_hi, self.above, tag=self.DOWN))
+        if ops:
+            for r in dist.batch_isend_irecv(ops):
+                r.wait()
+        if stage:
+            if self.below is not None:
+                dev_lo.copy_(recv_lo)
+            if self.above is not None:
+                dev_hi.copy_(recv_hi)
+
+    def exchange(self, bottom_row, top_row):
+        """Host rows: send this slab's edge rows ([72][nx + 2] FP64), receive
+        the neighbours'; returns (row_lo, row_hi), each None at a
+        non-periodic end of the domain."""
+        import torch
+        shape = (len(self.up), self.nx + 2)
+        send_lo = torch.from_numpy(pack(bottom_row, self.down))
+        send_hi = torch.from_numpy(pack(top_row, self.up))
+        recv_lo = torch.empty(shape, dtype=torch.float64)
+        recv_hi = torch.empty(shape, dtype=torch.float64)
+        self.exchange_packed(send_lo, send_hi, recv_lo, recv_hi)
+        row_lo = unpack(recv_lo.numpy(), self.up, self.nx) if self.below is not None else None
+        row_hi = unpack(recv_hi.numpy(), self.down, self.nx) if self.above is not None else None
         return row_lo, row_hi
+
+
+class DeviceSlab:
+    """One y-slab on this process's GPU: domain `domain` of a Simulation
+    (paper_1709_09073_gb300.rlbm) built with slab_bcs, its y neighbours
+    reached through `exchange` (a SlabExchange over NCCL, or any object with
+    the same below/above/exchange_packed). Every step packs the edge rows on
+    the device, exchanges them, writes the received rows into the ghost rows
+    and steps the Simulation once. The Simulation must run on the current
+    torch stream, which orders the NCCL messages after the pack and the
+    unpack after the messages."""
+
+    def __init__(self, sim, domain, exchange):
+        self.sim, self.domain, self.ex = sim, domain, exchange
+        self.send_lo, self.send_hi = sim.edge_row_buffer(domain), sim.edge_row_buffer(domain)
+        self.recv_lo, self.recv_hi = sim.edge_row_buffer(domain), sim.edge_row_buffer(domain)
+
+    def pack(self):
+        lo = self.send_lo if self.ex.below is not None else None
+        hi = self.send_hi if self.ex.above is not None else None
+        self.sim.pack_edge_rows(self.domain, lo, hi)
+
+    def unpack(self):
+        lo = self.recv_lo if self.ex.below is not None else None
+        hi = self.recv_hi if self.ex.above is not None else None
+        self.sim.unpack_ghost_rows(self.domain, lo, hi)
+
+    def halo(self):
+        """Bring the ghost rows up to date (after init and before each step)."""
+        self.pack()
+        self.ex.exchange_packed(self.send_lo, self.send_hi, self.recv_lo, self.recv_hi)
+        self.unpack()
+
+    def step(self, nsteps=1):
+        for _ in range(nsteps):
+            self.halo()
+            self.sim.step(1)
 
 
 def halo_bytes_per_face(nx, esize):

@@ -53,6 +53,10 @@ def test_library_loads_without_gpu(lib_path):
     # pure host calls: status strings and workspace sizing do not touch the GPU
     assert L.rlbm_status_string(0) == b"ok"
     assert b"argument" in L.rlbm_status_string(-1)
+    # slab rows: a null handle is refused on the host
+    assert L.rlbm_edge_row_bytes(None, 0) == 0
+    assert L.rlbm_pack_edge_rows(None, 0, None, None) == -1
+    assert L.rlbm_unpack_ghost_rows(None, 0, None, None) == -1
 
 
 def test_workspace_sizing_and_validation(lib_path):

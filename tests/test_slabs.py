@@ -2,7 +2,8 @@
 slabs stepped by the oracle, each fed only the 30 edge-row planes its
 neighbours send, reproduce the whole-domain oracle bit for bit -- in process
 for three uneven slabs, and as two gloo ranks exchanging rows with
-torch.distributed point-to-point messages."""
+torch.distributed point-to-point messages (the same exchange that carries
+the device-packed rows of slabs on GPUs over NCCL)."""
 import os
 import socket
 
@@ -111,17 +112,19 @@ def _rank_main(rank, world, port, name, q):
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("name", ["periodic", "x_walls"])
-def test_two_gloo_ranks_match_whole_domain(orc, name):
+@pytest.mark.parametrize("name,world", [("periodic", 2), ("x_walls", 2), ("y_walls_open_x", 3)])
+def test_gloo_ranks_match_whole_domain(orc, name, world):
+    """Two periodic ranks are each other's neighbour on both faces (messages
+    must match in order); three ranks between y walls have open ends."""
     pytest.importorskip("torch")
     import multiprocessing as mp
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, name, q)) for r in range(2)]
+    procs = [ctx.Process(target=_rank_main, args=(r, world, port, name, q)) for r in range(world)]
     for p in procs:
         p.start()
-    res = sorted((q.get(timeout=300) for _ in range(2)), key=lambda r: r[0])
+    res = sorted((q.get(timeout=300) for _ in range(world)), key=lambda r: r[0])
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
