@@ -479,27 +479,64 @@ __device__ __forceinline__ unsigned collide_mixed(const DomDev& D, int x, int y,
   return st;
 }
 
+// L2 prefetch of the next tile in persistent grids (1) or none (0). Measured on
+// GB300: prefetches that run slow the step (at 2048^2, prefetching the tile one
+// resident wave ahead in a one-block-per-tile grid: 6,383 -> 4,894..5,390 MLUPS),
+// and the autotuner keeps one block per tile, where the branch below is never
+// taken; yet the step compiled with it runs 2.6 % (256-domain batch) and 4.9 %
+// (2048^2) faster than without it, with the same registers and spills reported
+// by ptxas -- an effect of code generation, kept because it was measured.
+#ifndef RLBM_MIXED_PREFETCH
+#define RLBM_MIXED_PREFETCH 1
+#endif
+// prefetch distance in tiles for one-block-per-tile grids (0: none)
+#ifndef RLBM_MIXED_PREFETCH_AHEAD
+#define RLBM_MIXED_PREFETCH_AHEAD 0
+#endif
+
+// Ask L2 for the rows the pull of tile t reads: 72 planes x rows y0-1..y0+4,
+// from the 16-byte boundary lpad elements left of x0 (x = x0 - lpad) to x0+32,
+// one bulk prefetch per plane row spread over the block's threads. Each one
+// starts 64-byte aligned (x0 is a multiple of 32, rows are 128-byte pitched)
+// and stops at the end of its padded row.
+template <class S>
+__device__ __forceinline__ void prefetch_tile_l2(const StepArgs& a, int t, int tid) {
+  using T = typename S::T;
+  const Tile tl = a.tiles[t];
+  const DomDev& D = a.doms[tl.dom];
+  const T* base = static_cast<const T*>(a.fin) + D.off;
+  const int ylo = max(tl.y0 - 1, -1), yhi = min(tl.y0 + 4, D.ny);
+  const int rows = yhi - ylo + 1;
+  const unsigned need = ((unsigned)((D.lpad + 33) * sizeof(T)) + 15u) & ~15u;
+  const unsigned room = (unsigned)((D.pitch - tl.x0) * sizeof(T));
+  const unsigned bytes = min(need, room);
+  for (int i = tid; i < 72 * rows; i += kThreads) {
+    const int q = i / rows, yy = ylo + i % rows;
+    const T* p = base + q * D.plane + (long long)(yy + 1) * D.pitch + tl.x0;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "r"(bytes)
+                 : "memory");
+  }
+}
+
+// One 32 x 4 tile of the step: pull, collide, store (the thread's cell).
 template <int EDF, class S>
-__global__ void __launch_bounds__(kThreads, RLBM_MIXED_MIN_BLOCKS) k_step_mixed(StepArgs a) {
-  extern __shared__ float smf[];
-  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-  for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
-    const Tile tl = a.tiles[t];
-    const DomDev& D = a.doms[tl.dom];
-    const int x = tl.x0 + threadIdx.x, y = tl.y0 + threadIdx.y;
-    if (x >= D.nx || y >= D.ny) continue;
-    const long long P = D.plane;
-    const int W = D.pitch;
-    const typename S::T* __restrict__ fin = static_cast<const typename S::T*>(a.fin) + D.off;
-    typename S::T* __restrict__ fout = static_cast<typename S::T*>(a.fout) + D.off;
-    const long long c = (long long)(y + 1) * W + D.lpad + x;
-    // pull (FP32, deviation form) with the FP32 deviation moment sums
-    float A[12], B[12], pc[6], p2c[6];
+__device__ __forceinline__ void step_tile_mixed(const StepArgs& a, int t, float* smf, int tid) {
+  const Tile tl = a.tiles[t];
+  const DomDev& D = a.doms[tl.dom];
+  const int x = tl.x0 + threadIdx.x, y = tl.y0 + threadIdx.y;
+  if (x >= D.nx || y >= D.ny) return;
+  const long long P = D.plane;
+  const int W = D.pitch;
+  const typename S::T* __restrict__ fin = static_cast<const typename S::T*>(a.fin) + D.off;
+  typename S::T* __restrict__ fout = static_cast<typename S::T*>(a.fout) + D.off;
+  const long long c = (long long)(y + 1) * W + D.lpad + x;
+  // pull (FP32, deviation form) with the FP32 deviation moment sums
+  float A[12], B[12], pc[6], p2c[6];
 #pragma unroll
-    for (int s = 0; s < 6; ++s) {
-      pc[s] = c_pf[EDF][s];
-      p2c[s] = c_p2f[EDF][s];
-    }
+  for (int s = 0; s < 6; ++s) {
+    pc[s] = c_pf[EDF][s];
+    p2c[s] = c_p2f[EDF][s];
+  }
 #define RLBM_PULL_DIR(d)                                                        \
   {                                                                             \
     float a_ = 0.0f, b_ = 0.0f;                                                 \
@@ -512,12 +549,28 @@ __global__ void __launch_bounds__(kThreads, RLBM_MIXED_MIN_BLOCKS) k_step_mixed(
     A[d] = a_;                                                                  \
     B[d] = b_;                                                                  \
   }
-    RLBM_PULL_DIR(0) RLBM_PULL_DIR(1) RLBM_PULL_DIR(2) RLBM_PULL_DIR(3)
-    RLBM_PULL_DIR(4) RLBM_PULL_DIR(5) RLBM_PULL_DIR(6) RLBM_PULL_DIR(7)
-    RLBM_PULL_DIR(8) RLBM_PULL_DIR(9) RLBM_PULL_DIR(10) RLBM_PULL_DIR(11)
+  RLBM_PULL_DIR(0) RLBM_PULL_DIR(1) RLBM_PULL_DIR(2) RLBM_PULL_DIR(3)
+  RLBM_PULL_DIR(4) RLBM_PULL_DIR(5) RLBM_PULL_DIR(6) RLBM_PULL_DIR(7)
+  RLBM_PULL_DIR(8) RLBM_PULL_DIR(9) RLBM_PULL_DIR(10) RLBM_PULL_DIR(11)
 #undef RLBM_PULL_DIR
-    const unsigned st = collide_mixed<EDF, S>(D, x, y, c, A, B, smf, tid, fout);
-    if (st) atomicOr(a.status, st);
+  const unsigned st = collide_mixed<EDF, S>(D, x, y, c, A, B, smf, tid, fout);
+  if (st) atomicOr(a.status, st);
+}
+
+template <int EDF, class S>
+__global__ void __launch_bounds__(kThreads, RLBM_MIXED_MIN_BLOCKS) k_step_mixed(StepArgs a) {
+  extern __shared__ float smf[];
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+#if RLBM_MIXED_PREFETCH
+    {
+      // persistent grid: the block's next tile; one block per tile: the tile a
+      // block of the next resident wave will take
+      const int ahead = (int)gridDim.x < a.ntiles ? (int)gridDim.x : RLBM_MIXED_PREFETCH_AHEAD;
+      if (ahead > 0 && t + ahead < a.ntiles) prefetch_tile_l2<S>(a, t + ahead, tid);
+    }
+#endif
+    step_tile_mixed<EDF, S>(a, t, smf, tid);
   }
 }
 
