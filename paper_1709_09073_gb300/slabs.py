@@ -52,7 +52,10 @@ def slab_bounds(ny, nranks):
 
 
 def neighbours(rank, nranks, periodic_y):
-    """(rank below, rank above); None at a non-periodic end of the domain."""
+    """(rank below, rank above); None at a non-periodic end of the domain, and
+    both None for a single slab (it keeps the domain's own y sides)."""
+    if nranks == 1:
+        return None, None
     below = rank - 1 if rank > 0 else (nranks - 1 if periodic_y else None)
     above = rank + 1 if rank < nranks - 1 else (0 if periodic_y else None)
     return below, above
@@ -61,7 +64,9 @@ def neighbours(rank, nranks, periodic_y):
 def slab_bcs(bc, rank, nranks):
     """Boundary conditions of a slab: x sides as the domain's; a y side that
     borders another slab gets zero-gradient, a placeholder never read because
-    that row is supplied by the neighbour."""
+    that row is supplied by the neighbour. A single slab is the whole domain."""
+    if nranks == 1:
+        return tuple(bc)
     xlo, xhi, ylo, yhi = bc
     periodic_y = ylo == 0
     ZG = 1

@@ -1,9 +1,10 @@
 """The y-slab decomposition plan (paper_1709_09073_gb300/slabs.py) on CPU:
 slabs stepped by the oracle, each fed only the 30 edge-row planes its
-neighbours send, reproduce the whole-domain oracle bit for bit -- in process
-for three uneven slabs, and as two gloo ranks exchanging rows with
-torch.distributed point-to-point messages (the same exchange that carries
-the device-packed rows of slabs on GPUs over NCCL)."""
+neighbours send, reproduce the whole-domain oracle bit for bit -- in process for three uneven
+slabs (and for one slab, which keeps the domain's own y sides), and as two or
+three gloo ranks exchanging rows with torch.distributed point-to-point
+messages (the same exchange that carries the device-packed rows of slabs on
+GPUs over NCCL)."""
 import os
 import socket
 
@@ -31,6 +32,13 @@ def test_plan():
     b = slabs.slab_bounds(11, 3)
     assert b == [(0, 4), (4, 8), (8, 11)]
     assert slabs.neighbours(0, 3, False) == (None, 1) and slabs.neighbours(2, 3, True) == (1, 0)
+    # two periodic ranks border each other on both faces; one slab is the whole domain
+    assert slabs.neighbours(0, 2, True) == (1, 1)
+    assert slabs.neighbours(0, 1, True) == (None, None)
+    assert slabs.slab_bcs((0, 0, 0, 0), 0, 1) == (0, 0, 0, 0)
+    assert slabs.slab_bcs((0, 0, 0, 0), 0, 2) == (0, 0, 1, 1)
+    assert slabs.slab_bcs((2, 2, 2, 2), 1, 3) == (2, 2, 1, 1)
+    assert slabs.slab_bcs((2, 2, 2, 2), 2, 3) == (2, 2, 1, 2)
     with pytest.raises(ValueError):
         slabs.slab_bounds(2, 3)
 
@@ -68,9 +76,10 @@ class _Slab:
         self.m = mo[[0, 2, 3]].copy()
 
 
+@pytest.mark.parametrize("k", [1, 3])
 @pytest.mark.parametrize("name", list(CASES))
-def test_three_uneven_slabs_in_process(orc, name):
-    nx, ny, steps, k = 14, 11, 6, 3
+def test_uneven_slabs_in_process(orc, name, k):
+    nx, ny, steps = 14, 11, 6
     spec, init = _setup(orc, name, nx, ny)
     periodic_y = spec.bc[2] == PERIODIC
     parts = [_Slab(orc, spec, init, r, k) for r in range(k)]
