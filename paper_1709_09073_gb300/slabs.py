@@ -102,17 +102,20 @@ class SlabExchange:
         below, send_hi: the top row's for the slab above) and receive the
         neighbours' into recv_lo (from below) and recv_hi (from above). Torch
         tensors on the process group's device (CPU for gloo, the rank's GPU
-        for NCCL); faces toward a non-periodic end of the domain are skipped.
+        for NCCL); faces toward a non-periodic end of the domain are skipped
+        and may be None.
         Both sends are posted before both receives, rows travelling up first
         on either side, so that two ranks that are each other's neighbour on
         both faces match their messages in order as well as by tag. Device
         faces over a host-only backend (gloo) are staged through host memory."""
         import torch.distributed as dist
-        stage = send_lo.is_cuda and dist.get_backend() == "gloo"
+        faces = [t for t in (send_lo, send_hi, recv_lo, recv_hi) if t is not None]
+        stage = bool(faces) and faces[0].is_cuda and dist.get_backend() == "gloo"
         if stage:
             dev_lo, dev_hi = recv_lo, recv_hi
-            send_lo, send_hi = send_lo.cpu(), send_hi.cpu()
-            recv_lo, recv_hi = send_lo.new_empty(send_lo.shape), send_hi.new_empty(send_hi.shape)
+            host = lambda t: t.cpu() if t is not None else None
+            send_lo, send_hi = host(send_lo), host(send_hi)
+            recv_lo, recv_hi = host(recv_lo), host(recv_hi)
         ops = []
         if self.above is not None:
             ops.append(dist.P2POp(dist.isend, send_hi, self.above, tag=self.UP))

@@ -104,6 +104,7 @@ def _free_port():
 def _rank_main(rank, world, port, name, q):
     import sys
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import torch
     import torch.distributed as dist
     from oracle import oracle as orc
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
@@ -114,7 +115,17 @@ def _rank_main(rank, world, port, name, q):
         part = _Slab(orc, spec, init, rank, world)
         ex = slabs.SlabExchange(rank, world, nx, spec.bc[2] == PERIODIC)
         for _ in range(steps):
-            lo, hi = ex.exchange(*part.edges())
+            if world == 3:  # packed faces, None toward the domain's ends
+                bottom, top = part.edges()
+                f = lambda row, planes, keep: (torch.from_numpy(slabs.pack(row, planes)) if keep else None)
+                send_lo, send_hi = f(bottom, ex.down, ex.below is not None), f(top, ex.up, ex.above is not None)
+                recv_lo = torch.empty((30, nx + 2), dtype=torch.float64) if ex.below is not None else None
+                recv_hi = torch.empty((30, nx + 2), dtype=torch.float64) if ex.above is not None else None
+                ex.exchange_packed(send_lo, send_hi, recv_lo, recv_hi)
+                lo = slabs.unpack(recv_lo.numpy(), ex.up, nx) if recv_lo is not None else None
+                hi = slabs.unpack(recv_hi.numpy(), ex.down, nx) if recv_hi is not None else None
+            else:
+                lo, hi = ex.exchange(*part.edges())
             part.step(lo, hi)
         q.put((rank, part.y0, part.f))
     finally:
