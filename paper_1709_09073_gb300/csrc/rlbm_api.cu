@@ -327,7 +327,8 @@ int slab_rows(rlbm_handle h, int domain, void* lo, void* hi, int unpack) {
   a.face[0] = lo;
   a.face[1] = hi;
   const long long n = 2LL * kSlabPlanes * (D.nx + 2);
-  const int grid = (int)std::min<long long>((n + 255) / 256, 1216);
+  // one element per thread, at most 8 blocks of 256 per SM (152 SMs); the loop strides beyond
+  const int grid = (int)std::min<long long>((n + 255) / 256, 8 * 152);
   switch (es) {
     case 8: k_rows<unsigned long long><<<grid, 256, 0, h->stream>>>(a); break;
     case 4: k_rows<unsigned><<<grid, 256, 0, h->stream>>>(a); break;
