@@ -305,11 +305,9 @@ FP64_FLOPS_PER_CELL = 2 * 872 + 308 + 202
 FP64_INSTR_PER_CELL = 872 + 308 + 202
 
 
-def cpu_baseline(wl, budget_s=15.0):
-    """The FP64 oracle, as it stands, on the host cores: whole domains of the
-    workload, one step each, until the time budget is used."""
-    from oracle import oracle as O
-    O.build()
+def _oracle_rate(O, wl, budget_s):
+    """Cells per second of one oracle step over whole domains of the workload,
+    in order, until the time budget is used; (rate, domains, cells)."""
     done_cells, t_used, ndom = 0, 0.0, 0
     for d, s in zip(wl.domains, wl.init):
         dom = O.domain(d.nx, d.ny, d.tau, d.edf, d.bc, d.t_wall)
@@ -321,9 +319,37 @@ def cpu_baseline(wl, budget_s=15.0):
         ndom += 1
         if t_used > budget_s:
             break
-    return {"value": round(done_cells / t_used / 1e6, 4), "unit": UNIT, "cores": O.num_threads(),
-            "kind": "oracle",
-            "sample": "1 step of each of the first %d domains (%d cells) of the workload" % (ndom, done_cells)}
+    return done_cells / t_used, ndom, done_cells
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return None
+
+
+def cpu_baseline(wl, budget_s=15.0):
+    """The FP64 oracle, as it stands, on the host cores (OpenMP over rows),
+    and once more on one thread with a third of the budget."""
+    from oracle import oracle as O
+    O.build()
+    cores = O.num_threads()
+    rate, ndom, cells = _oracle_rate(O, wl, budget_s)
+    O.set_num_threads(1)
+    try:
+        rate1, ndom1, cells1 = _oracle_rate(O, wl, budget_s / 3)
+    finally:
+        O.set_num_threads(cores)
+    return {"value": round(rate / 1e6, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "1 step of each of the first %d domains (%d cells) of the workload" % (ndom, cells),
+            "single_thread": {"value": round(rate1 / 1e6, 4), "unit": UNIT, "cores": 1,
+                              "sample": "1 step of each of the first %d domains (%d cells)" % (ndom1, cells1)},
+            "cpu_model": cpu_model(), "nproc": os.cpu_count()}
 
 
 def run_profile_case(args):

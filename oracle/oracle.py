@@ -89,6 +89,8 @@ def lib():
         L.orc_init.argtypes = [ctypes.POINTER(Domain), ctypes.c_int, _D, _D, _D, _D, _D, _D]
         L.orc_fields.argtypes = [ctypes.POINTER(Domain), _D, _D, ctypes.c_int, _D]
         L.orc_num_threads.restype = ctypes.c_int
+        L.orc_set_num_threads.argtypes = [ctypes.c_int]
+        L.orc_set_num_threads.restype = None
         _lib = L
     return _lib
 
@@ -256,3 +258,8 @@ def diagnostics(dom, f, macro_in=None, streamed=True):
 
 def num_threads():
     return lib().orc_num_threads()
+
+
+def set_num_threads(n):
+    """Threads of later oracle calls (OpenMP over rows; 1 without OpenMP)."""
+    lib().orc_set_num_threads(int(n))

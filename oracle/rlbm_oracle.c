@@ -49,6 +49,14 @@ int orc_num_threads(void) {
 #endif
 }
 
+void orc_set_num_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
 /* Compensated (Neumaier) summation step. */
 static void neumaier_add(double *sum, double *comp, double x) {
   double t = *sum + x;

@@ -133,6 +133,8 @@ int orc_diagnostics(const orc_domain *D, const double *f_in, const double *macro
 
 /* Number of OpenMP threads the oracle uses (1 when built without OpenMP). */
 int orc_num_threads(void);
+/* Threads for later calls (n > 0); the timing of the CPU baseline runs it at 1. */
+void orc_set_num_threads(int n);
 
 #ifdef __cplusplus
 }
