@@ -1,7 +1,9 @@
 """The y-slab decomposition plan (paper_1709_09073_gb300/slabs.py) on CPU:
 slabs stepped by the oracle, each fed only the 30 edge-row planes its
-neighbours send, reproduce the whole-domain oracle bit for bit -- in process for three uneven
-slabs (and for one slab, which keeps the domain's own y sides), and as two or
+neighbours send, reproduce the whole-domain oracle bit for bit -- with periodic,
+fixed-temperature, zero-gradient and velocity-wall sides and a body force, in
+process for three uneven slabs (and for one slab, which keeps the domain's own
+y sides), and as two or
 three gloo ranks exchanging rows with torch.distributed point-to-point
 messages (the same exchange that carries the device-packed rows of slabs on
 GPUs over NCCL)."""
@@ -14,11 +16,17 @@ import pytest
 from paper_1709_09073_gb300 import slabs, workloads as W
 
 PERIODIC, ZG, WALL = W.PERIODIC, W.ZERO_GRADIENT, W.FIXED_T_WALL
+VW = W.VELOCITY_WALL
 CASES = {
     "periodic": ((PERIODIC,) * 4, (1.0,) * 4),
     "x_walls": ((WALL, WALL, PERIODIC, PERIODIC), (0.97, 1.04, 1.0, 1.0)),
     "y_walls_open_x": ((ZG, ZG, WALL, WALL), (1.0, 1.0, 1.03, 0.96)),
+    # velocity walls with a body force (Sec. 3.4): channel walls at the slab stack's
+    # ends, and walls on the x sides of every slab
+    "channel_force": ((PERIODIC, PERIODIC, VW, VW), (1.02,) * 4),
+    "x_velocity_walls": ((VW, VW, PERIODIC, PERIODIC), (1.02,) * 4),
 }
+FORCE = dict(accel=(2e-4, -1e-4), n_wall=1.05)
 
 
 def test_plan():
@@ -45,13 +53,18 @@ def test_plan():
 
 def _setup(orc, name, nx, ny):
     bc, tw = CASES[name]
-    spec = W.DomainSpec(nx, ny, 0.85, W.MJ, bc, tw)
+    extra = FORCE if VW in bc else {}
+    spec = W.DomainSpec(nx, ny, 0.85, W.MJ, bc, tw, **extra)
     init = W.random_domain_state(nx, ny, 77, W.MJ, u_amp=0.06)
     return spec, init
 
 
+def _domain(orc, spec, ny, bc):
+    return orc.domain(spec.nx, ny, spec.tau, spec.edf, bc, spec.t_wall, accel=spec.accel, n_wall=spec.n_wall)
+
+
 def _whole(orc, spec, init, steps):
-    dom = orc.domain(spec.nx, spec.ny, spec.tau, spec.edf, spec.bc, spec.t_wall)
+    dom = _domain(orc, spec, spec.ny, spec.bc)
     f, m, _ = orc.init(dom, init.kind, init.a, init.theta, init.ux, init.uy)
     f, m, _ = orc.run(dom, f, m, steps)
     return f
@@ -63,17 +76,21 @@ class _Slab:
         y0, y1 = slabs.slab_bounds(spec.ny, nranks)[rank]
         self.y0, self.y1 = y0, y1
         bc = slabs.slab_bcs(spec.bc, rank, nranks)
-        self.dom = orc.domain(spec.nx, y1 - y0, spec.tau, spec.edf, bc, spec.t_wall)
+        self.dom = _domain(orc, spec, y1 - y0, bc)
         cut = lambda a: np.ascontiguousarray(a[y0:y1])
         self.f, self.m, _ = orc.init(self.dom, init.kind, cut(init.a), cut(init.theta), cut(init.ux),
                                      cut(init.uy))
+        # velocity walls read the full six-plane state of the previous step
+        self.full = orc.has_velocity_wall(self.dom)
+        if self.full:
+            self.m, _ = orc.fields(self.dom, self.f, None, streamed=False)
 
     def edges(self):
         return self.orc.edge_row(self.dom, self.f, self.m, 0), self.orc.edge_row(self.dom, self.f, self.m, 1)
 
     def step(self, row_lo, row_hi):
         self.f, mo, _ = self.orc.step_rows(self.dom, self.f, self.m, row_lo, row_hi)
-        self.m = mo[[0, 2, 3]].copy()
+        self.m = mo.copy() if self.full else mo[[0, 2, 3]].copy()
 
 
 @pytest.mark.parametrize("k", [1, 3])
