@@ -174,3 +174,28 @@ def test_density_and_energy_closed_forms(orc, edf):
         # MJ at rest: eps = 2P = 2 n T
         if edf == 0:
             assert abs(out[5] - 2 * out[0] * out[1]) <= 1e-13 * out[5]
+
+
+@pytest.mark.parametrize("edf", [0, 1, 2])
+def test_feq_is_a_perfect_fluid_in_any_frame(orc, edf):
+    """Lorentz covariance of the lowest equilibrium moments. For a state
+    (theta, u, z) the discrete f^eq carries N^mu = n U^mu and T^{mu nu} =
+    (eps + P) U^mu U^nu - P eta^{mu nu}, with the rest-frame n = 2 pi theta^2
+    g_2(z) and eps = 2P = 4 pi theta^3 g_3(z) (Eq. 25). This checks the boosted
+    moments through the perfect-fluid form alone, not the Appendix formulas."""
+    p, w, c, s = orc.lattice(edf)
+    P = np.tile(p, 12)
+    pv = [P, P * np.repeat(c, 6), P * np.repeat(s, 6)]
+    eta = np.diag([1.0, -1.0, -1.0])
+    for th, ux, uy, z in [(1.0, 0.3, -0.2, 0.4), (0.8, -0.55, 0.1, 0.2), (1.3, 0.05, 0.62, 0.7)]:
+        fe = orc.feq(edf, th, ux, uy, z)
+        gam = 1.0 / math.sqrt(1.0 - ux * ux - uy * uy)
+        U = np.array([gam, gam * ux, gam * uy])
+        n = 2 * math.pi * th ** 2 * orc.g(edf, 2, z)
+        eps = 4 * math.pi * th ** 3 * orc.g(edf, 3, z)
+        pr = eps / 2
+        for a in range(3):
+            assert abs(np.sum(fe * pv[a]) - n * U[a]) <= 1e-13 * n * gam, (a, th, ux, uy)
+            for b in range(3):
+                ref = (eps + pr) * U[a] * U[b] - pr * eta[a, b]
+                assert abs(np.sum(fe * pv[a] * pv[b]) - ref) <= 1e-12 * (eps + pr) * gam ** 2, (a, b)
