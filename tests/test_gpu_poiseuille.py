@@ -67,3 +67,35 @@ def test_poiseuille_steady_state(R, orc):
     print("poiseuille ny %d: |du| %.2e of max u %.2e" % (ny, du, np.max(np.abs(ref[2]))))
     assert du <= 1e-14
     assert max(errors(out, ref)[:2]) <= 1e-12
+
+
+def test_poiseuille_grid_convergence_to_512(R):
+    """Sec. 3.4 at the paper's sizes L = 16..512 (tau = 3, a = 1e-8, MJ, FP64):
+    against the closed-form viscosity of a shear along a lattice axis,
+    nu = (tau - 1/2 + sqrt(3)/6)/4, the steady profile's eps_u falls as L^-2
+    (fitted slope -2 +- 0.1; the paper prints -2.037). Each channel starts from
+    the reference parabola and runs 6 (L + 1)^2 / nu steps."""
+    import math
+    tau, a = 3.0, 1e-8
+    nu = (tau - 0.5 + math.sqrt(3.0) / 6.0) / 4
+    sizes, errs = (16, 32, 64, 128, 256, 512), []
+    for L in sizes:
+        spec = W.DomainSpec(1, L, tau, W.MJ, (W.PERIODIC, W.PERIODIC, W.VELOCITY_WALL, W.VELOCITY_WALL),
+                            accel=(a, 0.0), n_wall=1.0)
+        y = np.arange(L, dtype=float)
+        ref = a / (2 * nu) * (y + 1) * (L - y)
+        one, zero = np.ones((L, 1)), np.zeros((L, 1))
+        sim = R.Simulation([spec], edf=W.MJ, storage=R.RLBM_F64)
+        sim.init(0, W.InitialState(W.INIT_N_THETA, one, one, ref[:, None].copy(), zero))
+        sim.step(int(6 * (L + 1) ** 2 / nu) + 2000)
+        ux = sim.moments(0, streamed=False)[2][:, 0]
+        sim.step(1000)
+        ux2 = sim.moments(0, streamed=False)[2][:, 0]
+        st = sim.sync_status()
+        sim.close()
+        assert st == 0
+        assert np.max(np.abs(ux2 - ux)) <= 1e-9 * np.max(ux)
+        errs.append(math.sqrt(np.sum((ux - ref) ** 2) / np.sum(ref ** 2)))
+    slope = np.polyfit(np.log(sizes), np.log(errs), 1)[0]
+    print("poiseuille eps_u", ["%.3e" % e for e in errs], "slope %.3f" % slope)
+    assert abs(slope + 2.0) <= 0.1

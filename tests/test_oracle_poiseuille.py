@@ -3,8 +3,12 @@ the oracle: a uniform fluid under acceleration a gains velocity a per step
 (Newton's law for the u + a tau momentum update); a fluid at rest between
 velocity walls at its own density and temperature stays at rest; the forced
 channel flow reaches a steady parabola that vanishes at the wall nodes (the
-ghost rows) with a curvature giving the Taylor-Green viscosity law
-nu = (tau - 0.2546) / 4 to within 2 %."""
+ghost rows) with the curvature a/(2 nu) of the closed-form viscosity of a shear
+along a lattice axis, nu = (tau - 1/2 + sqrt(3)/6)/4 (the numerical viscosity
+of the bilinear streaming for this orientation; the Taylor-Green law of
+Sec. 3.2 belongs to the diagonal orientation and is 1.6 % lower at tau = 3)."""
+import math
+
 import numpy as np
 import pytest
 
@@ -39,7 +43,7 @@ def test_rest_between_velocity_walls(orc, edf):
 
 def test_poiseuille_parabola(orc):
     tau, a, ny = 3.0, 1e-8, 23
-    nu = (tau - 0.2546) / 4
+    nu = (tau - 0.5 + math.sqrt(3.0) / 6.0) / 4
     dom = orc.domain(1, ny, tau, 0, VW, accel=(a, 0.0), n_wall=1.0)
     one, zero = np.ones((ny, 1)), np.zeros((ny, 1))
     f, m, _ = orc.init(dom, 0, one, one, zero, zero)
@@ -52,5 +56,6 @@ def test_poiseuille_parabola(orc):
     assert np.max(np.abs(np.polyval(c, y) - ux)) <= 1e-3 * ux.max()   # a parabola
     lo, hi = np.sort(np.roots(c))
     assert abs(lo + 1.0) <= 0.05 and abs(hi - ny) <= 0.05           # zero at the wall nodes
-    assert abs(-a / (2 * c[0]) / nu - 1.0) <= 0.02                    # curvature a / (2 nu)
+    print("channel nu / axis-shear nu - 1 = %.2e" % (-a / (2 * c[0]) / nu - 1.0))
+    assert abs(-a / (2 * c[0]) / nu - 1.0) <= 3e-3                    # curvature a / (2 nu)
     assert np.allclose(ux, ux[::-1], rtol=1e-12, atol=0)              # symmetric channel

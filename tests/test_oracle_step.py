@@ -1,7 +1,6 @@
 """Pins of the oracle's time step: streaming (Eqs. 17-18), relaxation (Eq. 3),
-boundary ghosts, conservation, symmetry and the paper's viscosity law."""
-import math
-
+boundary ghosts, conservation and symmetry. The viscosity law is pinned in
+test_oracle_transport.py."""
 import numpy as np
 import pytest
 
@@ -144,29 +143,3 @@ def test_hot_wall_heats_fluid(orc):
     out, _ = orc.fields(dom, f, m)
     assert out[1][:, -1].mean() > 1.0 + 1e-4      # next to the hot wall
     assert abs(out[1][:, 0].mean() - 1.0) < out[1][:, -1].mean() - 1.0
-
-
-@pytest.mark.slow
-def test_taylor_green_viscosity_law(orc):
-    """Sec. 3.2, Eqs. (29)-(31): sigma_{u^2} decays as exp(-16 pi^2 nu t / L^2) with
-    nu_eff = (tau - 0.2546)/4. At L = 48 the lattice correction of the decay rate is
-    O((2 pi/L)^2) ~ 2 %, so the fit is accepted within 3 %."""
-    L = 48
-    for tau in (0.8, 1.4):
-        wl = W.taylor_green(L=L, u0=0.005, tau=tau, steps=0)
-        d, s = wl.domains[0], wl.init[0]
-        dom = orc.domain(d.nx, d.ny, d.tau, d.edf)
-        f, macro, _ = orc.init(dom, s.kind, s.a, s.theta, s.ux, s.uy)
-        ts, sig = [], []
-        for t in range(0, 121, 20):
-            if t:
-                f, macro, st = orc.run(dom, f, macro, 20)
-            out, _ = orc.fields(dom, f, macro, streamed=False)
-            u2 = out[2] ** 2 + out[3] ** 2
-            ts.append(t)
-            sig.append(math.sqrt(np.mean((u2 - u2.mean()) ** 2)))
-        ts, sig = np.array(ts[1:]), np.log(np.array(sig[1:]))
-        slope = np.polyfit(ts, sig, 1)[0]
-        nu = -slope * L * L / (16 * math.pi ** 2)
-        nu_law = 0.25 * (tau - 0.2546)
-        assert abs(nu - nu_law) <= 0.03 * nu_law, (tau, nu, nu_law)
