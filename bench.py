@@ -11,8 +11,10 @@ uniform in 32..512, seed 20260101), MJ fifth-order equilibrium, tau swept
 0.55..2.0, amplitudes 0.005..0.05 c, FP32 populations stored as deviations
 from each domain's rest equilibrium, one launch per step over
 a tile work list, autotuned grid, steps replayed from a CUDA graph. Under
-torchrun each rank runs its own independently seeded batch (weak scaling, no
-data-path collective); rank 0 prints one JSON line.
+torchrun the batch's domains are split over the ranks by cell count (strong
+scaling; --scaling weak gives every rank its own seeded batch instead). Ranks
+share no data: only the timing (max) and the cell count (sum) are reduced, and
+rank 0 prints one JSON line.
 """
 import argparse
 import json
@@ -28,12 +30,14 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-from paper_1709_09073_gb300 import workloads as W  # noqa: E402
+from paper_1709_09073_gb300 import partition, workloads as W  # noqa: E402
 
 METRIC = "lattice updates/s (MLUPS) FP64 vs mixed+batched on 1 GB300; % roofline"
 UNIT = "MLUPS"
 BYTES_PER_CELL = {0: 1152, 1: 576, 2: 288, 3: 288, 4: 576}   # 2 x 72 x element size
 STORAGE_NAME = {0: "f64", 1: "f32", 2: "bf16dev", 3: "f16dev", 4: "f32dev"}
+# the mixed step's variants (rlbm_select_kernel) by the kernel each launches
+KERNEL_NAMES = {0: "k_step_mixed", 1: "k_step_mixed_tma", 2: "k_step_lean", 3: "k_step_lean2"}
 
 
 def dist_env():
@@ -49,11 +53,6 @@ def peaks():
         d = json.load(open(p))
         return float(d.get("hbm_gbs", 6800.0)), "measured"
     return 6800.0, "fallback"
-
-
-# FP64 pipe: 2 FMA per clock per SM on GB300 (1.19 TFLOP/s measured with an FMA
-# chain at 2070 MHz); the ALU roofline uses 152 SMs x 2 FMA x 2 flop x SM clock.
-FP64_FLOP_PER_CLK_SM = 4.0
 
 
 class ClockSampler:
@@ -126,11 +125,15 @@ def timed_steps(sim, steps, torch):
     return e0.elapsed_time(e1) / 1e3
 
 
-def rank_workload(rank):
-    """The batch one rank advances: its own independently seeded set of domains
-    (the domains are independent problems, so ranks share no data; per-rank work
-    is fixed as the rank count grows: weak scaling)."""
-    return W.batched_taylor_green(seed=20260101 + rank)
+def rank_workload(rank, world=1, scaling="strong"):
+    """The batch one rank advances. strong: the one 256-domain batch split over
+    the ranks by cell count (longest first, to the least-loaded rank), so the
+    total work is fixed as the rank count grows; weak: every rank its own
+    independently seeded batch, so the per-rank work is fixed. The domains are
+    independent problems either way: ranks share no data."""
+    if scaling == "weak":
+        return W.batched_taylor_green(seed=20260101 + rank)
+    return partition.shard(W.batched_taylor_green(seed=20260101), rank, world)
 
 
 def over_ranks(x, world, torch, op="max", device="cuda"):
@@ -175,7 +178,8 @@ def run_native(args):
         dist.init_process_group("nccl")
     build.build()
     rlbm.load()
-    wl = rank_workload(rank)
+    pipes = rlbm.pipe_peaks()  # measured FMA-chain throughput: the ALU ceilings of the roofline
+    wl = rank_workload(rank, world, args.scaling)
     cells = wl.cells
     total_cells = over_ranks(cells, world, torch, "sum")  # units all ranks process per step
     storage = rlbm.RLBM_F32DEV
@@ -196,37 +200,39 @@ def run_native(args):
     bpc = BYTES_PER_CELL[storage]
     achieved = bpc * cells / per_launch / 1e9
     hbm_peak, peak_kind = peaks()
-    tr = traffic_record("k_step_mixed_f32dev_mj")
+    kname = KERNEL_NAMES[sim.select_kernel()]
+    tr = traffic_record("%s_f32dev_mj" % kname)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(achieved / hbm_peak, 4),
                 "traffic": round(tr * cells) if tr else None,
-                "peak_source": peak_kind, "kernel": "k_step_mixed<MJ, F32Dev>",
+                "peak_source": peak_kind, "kernel": "%s<MJ, F32Dev>" % kname,
                 "algorithmic_bytes_per_cell": bpc}
     launches = sim.last_step_info()[1]
 
-    # end to end through the public API with host buffers: fields uploaded from
-    # pinned host memory, every step followed by a status read-back, fields
-    # read back to pinned host memory at the end
-    pinned = []
-    for s in wl.init:
-        pinned.append([torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
-                       for x in (s.a, s.theta, s.ux, s.uy)])
+    # end to end through the public API with host buffers: the packed fields of
+    # every domain copied from pinned host memory and initialised in one call
+    # (rlbm_init_all), every step followed by a status read-back, the packed
+    # fields of every domain read back (rlbm_moments_all) into pinned memory;
+    # the device buffers they pass through are allocated before the clock starts
+    pinned = [torch.from_numpy(np.concatenate([getattr(s, k).reshape(-1) for s in wl.init])).pin_memory()
+              for k in ("a", "theta", "ux", "uy")]
+    dev_in = [torch.empty(cells, dtype=torch.float64, device="cuda") for _ in range(4)]
+    dev_out = [torch.empty(cells, dtype=torch.float64, device="cuda") for _ in range(5)]
+    out_host = [torch.empty(cells, dtype=torch.float64).pin_memory() for _ in range(5)]
     e2e_steps = max(1, args.steps)  # the K steps of the device-timed region
-    out_host = [[torch.empty((d.ny, d.nx), dtype=torch.float64).pin_memory() for _ in range(5)]
-                for d in wl.domains]
+    kind = wl.init[0].kind
     barrier(world)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for i, (d, s) in enumerate(zip(wl.domains, wl.init)):
-        dev = [x.to("cuda", non_blocking=True) for x in pinned[i]]
-        sim.init(i, W.InitialState(s.kind, *dev))
+    for d, h in zip(dev_in, pinned):
+        d.copy_(h, non_blocking=True)
+    sim.init_all(kind, *dev_in)
     for _ in range(e2e_steps):
         sim.step(1)
         sim.sync_status()
-    for i in range(len(wl.domains)):
-        outs = sim.moments(i, on_device=True)
-        for o, h in zip(outs, out_host[i]):
-            h.copy_(o, non_blocking=True)
+    sim.moments_all(out=dev_out)
+    for o, h in zip(dev_out, out_host):
+        h.copy_(o, non_blocking=True)
     torch.cuda.synchronize()
     te = time.perf_counter() - t0
     te = barrier_max(te, world, torch)
@@ -234,10 +240,10 @@ def run_native(args):
     d2h = 5 * 8 * cells + 4 * e2e_steps
     e2e = {"value": round(total_cells * e2e_steps / te / 1e6, 2), "unit": UNIT,
            "h2d_bytes_per_step": int(h2d / e2e_steps), "d2h_bytes_per_step": int(d2h / e2e_steps),
-           "steps": e2e_steps, "what": "upload fields -> rlbm_init -> (rlbm_step(1) + status read) x K -> "
-                                       "rlbm_moments to pinned host"}
+           "steps": e2e_steps, "what": "packed fields from pinned host -> rlbm_init_all -> "
+                                       "(rlbm_step(1) + status read) x K -> rlbm_moments_all -> pinned host"}
     sim.close()
-    del sim
+    del sim, dev_in, dev_out
 
     # the plain FP64 form on the same workload (the comparison the metric names)
     fp64 = None
@@ -250,21 +256,22 @@ def run_native(args):
         t64 = barrier_max(timed_steps(sim64, k64, torch), world, torch)
         v64 = total_cells * k64 / t64 / 1e6
         flops_per_cell = FP64_FLOPS_PER_CELL
-        clk = (clocks or {}).get("sm_mhz") or 2070.0
-        alu_peak = 152 * FP64_FLOP_PER_CLK_SM * clk * 1e6 / 1e12
+        alu_peak = pipes["fp64_flops"] / 1e12
+        instr_peak = pipes["fp64_flops"] / 2 / 1e9  # DFMA, DADD and DMUL issue at one rate
         ach = flops_per_cell * cells / (t64 / k64) / 1e12
+        ach_i = FP64_INSTR_PER_CELL * cells / (t64 / k64) / 1e9
         fp64 = {"value": round(v64, 2), "unit": UNIT, "steps": k64,
                 "ms_per_step": round(t64 / k64 * 1e3, 3),
                 "roofline": {"bound": "alu", "achieved": round(ach, 4), "peak": round(alu_peak, 4),
                              "unit": "TFLOP/s (FP64)", "frac": round(ach / alu_peak, 4),
                              "flops_per_cell": flops_per_cell,
-                             "peak_source": "152 SMs x 2 FP64 FMA/clk x median SM clock"},
+                             "peak_source": "measured: FP64 FMA-chain kernel on all %d SMs (rlbm_pipe_peaks)"
+                                            % pipes["sm_count"]},
                 # the pipe issues DADD and DMUL at the DFMA rate but they carry one
                 # flop: the instruction throughput of the FP64 pipe is its real bound
-                "fp64_pipe": {"instr_per_cell": FP64_INSTR_PER_CELL,
-                              "achieved": round(FP64_INSTR_PER_CELL * cells / (t64 / k64) / 1e9, 1),
-                              "peak": round(152 * 2 * clk * 1e6 / 1e9, 1), "unit": "G instr/s",
-                              "frac": round(FP64_INSTR_PER_CELL * cells / (t64 / k64) / (152 * 2 * clk * 1e6), 4)},
+                "fp64_pipe": {"instr_per_cell": FP64_INSTR_PER_CELL, "achieved": round(ach_i, 1),
+                              "peak": round(instr_peak, 1), "unit": "G instr/s",
+                              "frac": round(ach_i / instr_peak, 4)},
                 "hbm_achieved_gbs": round(1152 * cells / (t64 / k64) / 1e9, 1)}
         sim64.close()
 
@@ -280,17 +287,26 @@ def run_native(args):
         line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": round(t / args.steps * 1e3, 4), "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32 (double-float totals, Landau residual, n, eps; no FP64 instruction)",
+                "scaling": args.scaling, "vs_baseline": None,
+                "dtype": "f32 (double-float totals, Landau residual, n, eps; no FP64 instruction)",
                 "data": "synthetic",
                 "config": {"workload": wl.name, "domains": len(wl.domains), "cells_per_gpu": cells,
                            "cells_all_ranks": int(total_cells),
-                           "sides": "uniform 32..512 (seed 20260101 + rank)", "tau": "0.55..2.0",
+                           "sides": ("uniform 32..512 (seed 20260101), split over ranks by cell count"
+                                     if args.scaling == "strong" else "uniform 32..512 (seed 20260101 + rank)"),
+                           "tau": "0.55..2.0",
                            "u0": "0.005..0.05", "edf": "MJ", "order": 5,
                            "storage": "f32dev (FP32 populations as relative deviations from the rest equilibrium)",
                            "grid": grid, "l2": "inputs larger than L2 (%.1f GB of populations)"
-                           % (2 * 288 * cells / 1e9), "parallelism": "independent domains per GPU"},
+                           % (2 * 288 * cells / 1e9),
+                           "parallelism": ("one batch, whole domains per GPU by cell count (no collective)"
+                                           if args.scaling == "strong" else
+                                           "an independent batch per GPU (no collective)")},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clocks, "fp64": fp64, "other_configs": others, "status": status}
+                "clocks": clocks, "fp64": fp64, "other_configs": others, "status": status,
+                "pipe_peaks": {"fp64_tflops": round(pipes["fp64_flops"] / 1e12, 4),
+                               "fp32_tflops": round(pipes["fp32_flops"] / 1e12, 3),
+                               "sm_count": pipes["sm_count"], "how": "rlbm_pipe_peaks: FMA chains, best of 3"}}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -398,7 +414,7 @@ def run_other_configs(args, hbm_peak):
         ach = bpc * wl.cells / (t / k) / 1e9
         out[name] = {"value": round(wl.cells * k / t / 1e6, 2), "unit": UNIT, "steps": k,
                      "ms_per_step": round(t / k * 1e3, 3), "cells": wl.cells, "status": st,
-                     "kernel": "k_step_f64" if storage == rlbm.RLBM_F64 else "k_step_mixed",
+                     "kernel": "k_step_f64" if storage == rlbm.RLBM_F64 else KERNEL_NAMES[sim.select_kernel()],
                      "hbm": {"achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
                              "frac": round(ach / hbm_peak, 4), "algorithmic_bytes_per_cell": bpc}}
         sim.close()
@@ -529,6 +545,9 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--scaling", choices=["strong", "weak"], default="strong",
+                    help="strong: split the one batch over the ranks by cell count; "
+                         "weak: an independently seeded batch per rank")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-extra", action="store_true",
@@ -536,12 +555,21 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--kernel", choices=["l1", "tma"], default="l1",
                     help="mixed step variant of --profile-case mixed")
+    ap.add_argument("--peaks", action="store_true",
+                    help="print the measured FP64/FP32 FMA throughput of the GPU and exit")
     ap.add_argument("--profile-case", choices=["mixed", "fp64"], default=None,
                     help="run a small single-domain case for ncu instead of the benchmark")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.profile_case:
+    if args.peaks:
+        from paper_1709_09073_gb300 import build, rlbm
+        build.build()
+        rlbm.load()
+        p = rlbm.pipe_peaks()
+        print(json.dumps({"fp64_tflops": round(p["fp64_flops"] / 1e12, 4),
+                          "fp32_tflops": round(p["fp32_flops"] / 1e12, 3), "sm_count": p["sm_count"]}))
+    elif args.profile_case:
         run_profile_case(args)
     elif args.impl == "reference":
         run_reference(args)

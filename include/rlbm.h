@@ -130,9 +130,19 @@ int rlbm_create(const rlbm_config *config, rlbm_handle *out);
  * a = n; RLBM_INIT_Z_THETA: a = fugacity z (MJ: z = n / (2 pi theta^2), Eq. 25).
  * Fields are [ny][nx] FP64 on host (on_device = 0) or device (1). Every domain
  * must be initialised before the first rlbm_step. Returns warning bits of the
- * fugacity solve, or an error. */
+ * fugacity solve, or an error. FP64 storage evaluates the fifth-order
+ * equilibrium (Eqs. 10-11) in FP64; the mixed storages in the collision's own
+ * FP32 deviation arithmetic. */
 int rlbm_init(rlbm_handle h, int domain, int kind, const double *a, const double *theta,
               const double *ux, const double *uy, int on_device);
+
+/* rlbm_init for every domain of the handle in one kernel launch: each field
+ * array holds the domains' [ny][nx] fields one after the other in domain
+ * order (sum of nx * ny values, FP64, host or device per on_device; host
+ * fields are staged through the spare population copy). Returns the warning
+ * bits of this call, RLBM_E_ARG, RLBM_E_UNSUPPORTED or RLBM_E_CUDA. */
+int rlbm_init_all(rlbm_handle h, int kind, const double *a, const double *theta, const double *ux,
+                  const double *uy, int on_device);
 
 /* Advance every domain by nsteps >= 0 fused stream-collide steps (Eqs. 3,
  * 17-18), asynchronously on the handle's stream (replayed from a captured CUDA
@@ -147,6 +157,12 @@ int rlbm_step(rlbm_handle h, int nsteps);
  * device per on_device). Host outputs are complete on return. */
 int rlbm_moments(rlbm_handle h, int domain, int streamed, double *n, double *theta, double *ux,
                  double *uy, double *z, int on_device);
+
+/* rlbm_moments for every domain in one kernel launch: outputs packed as the
+ * fields of rlbm_init_all (z may be NULL). Every domain must be initialised
+ * (RLBM_E_STATE otherwise). */
+int rlbm_moments_all(rlbm_handle h, int streamed, double *n, double *theta, double *ux, double *uy,
+                     double *z, int on_device);
 
 /* Diagnostic fields of domain `domain` (streamed as for rlbm_moments), FP64
  * [7][ny][nx] into `out` (host or device per on_device): the heat flux
@@ -209,23 +225,51 @@ int rlbm_unpack_ghost_rows(rlbm_handle h, int domain, const void *lo, const void
  * warnings raised while timing are discarded. */
 int rlbm_tune(rlbm_handle h, int repeats);
 
-/* Variants of the mixed-precision step kernel; both compute the same update
- * with the same arithmetic (identical results).
- *  RLBM_KERNEL_L1   each thread pulls its bilinear neighbours from global
- *                   memory through L1 and stores its 72 values (default);
- *  RLBM_KERNEL_TMA  a ring of TMA boxes (one direction's six shell planes of a
- *                   32 x 4 tile and its ring) staged in shared memory; FP32
- *                   storages also write the collided tile back with one bulk
- *                   tensor store. Needs the driver's tensor-map encoder and
- *                   domains at least 4 cells wide. */
+/* Variants of the mixed-precision step kernel; all compute the same update
+ * with the same arithmetic in the same order (identical results).
+ *  RLBM_KERNEL_L1    each thread pulls its bilinear neighbours from global
+ *                    memory through L1 and stores its 72 values (default);
+ *  RLBM_KERNEL_TMA   a ring of TMA boxes (one direction's six shell planes of a
+ *                    32 x 4 tile and its ring) staged in shared memory; FP32
+ *                    storages also write the collided tile back with one bulk
+ *                    tensor store. Needs the driver's tensor-map encoder and
+ *                    domains at least 4 cells wide;
+ *  RLBM_KERNEL_LEAN  the L1 pull with the tile's domain descriptor staged in
+ *                    shared memory, the collision's shell loop unrolled and
+ *                    the halo work confined to edge tiles and cells;
+ *  RLBM_KERNEL_LEAN2 the same with two adjacent cells of a row per thread,
+ *                    each plane row read by one aligned pair load and one
+ *                    single load. */
 #define RLBM_KERNEL_L1 0
 #define RLBM_KERNEL_TMA 1
+#define RLBM_KERNEL_LEAN 2
+#define RLBM_KERNEL_LEAN2 3
 
 /* Select the step kernel variant (kernel >= 0) or query it (kernel < 0).
  * Returns the variant now in use, RLBM_E_ARG for an unknown variant, or
- * RLBM_E_UNSUPPORTED for RLBM_KERNEL_TMA on FP64 storage or without TMA
- * descriptors. rlbm_tune may change the selection. */
+ * RLBM_E_UNSUPPORTED for RLBM_KERNEL_TMA, _LEAN or _LEAN2 on FP64 storage (it
+ * has one step kernel) or RLBM_KERNEL_TMA without TMA descriptors. rlbm_tune
+ * may change the selection. */
 int rlbm_select_kernel(rlbm_handle h, int kernel);
+
+/* Time limit of every wait of the TMA-staged step (RLBM_KERNEL_TMA) for a
+ * copy to land, in seconds; 0 or less restores the default of one second. A
+ * wait that runs out ends the step early with RLBM_W_DEVICE_TIMEOUT set (the
+ * step's results are then invalid; the handle stays usable), after letting the
+ * copies still in flight land (bounded by the default limit). Limits under a
+ * microsecond poll without suspending, so they run out on the first copy not
+ * yet landed: a failure-detection test uses that. The paper has no
+ * counterpart. Returns RLBM_OK or RLBM_E_ARG (NaN). */
+int rlbm_set_wait_limit(rlbm_handle h, double seconds);
+
+/* Measured FMA throughput of this GPU (the current device): the FP64 and FP32
+ * flop rates (FMA = 2 flops) of an FMA-chain kernel over every SM, best of
+ * three timed launches, and the SM count. These are the compute ceilings of
+ * the step kernels' roofline; the paper has no counterpart (it is a property
+ * of the machine, not of the method). Outputs are host pointers (sm_count may
+ * be null). Takes about two seconds; synchronises the device's work it
+ * launches. Returns RLBM_OK, RLBM_E_ARG or RLBM_E_CUDA. */
+int rlbm_pipe_peaks(double *fp64_flops, double *fp32_flops, int *sm_count);
 
 /* Wait for the handle's stream, return the warning bits accumulated since the
  * last call (and clear them), or RLBM_E_CUDA. */

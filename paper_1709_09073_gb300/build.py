@@ -15,7 +15,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "librlbm.so")
 # the mixed-precision kernels are split by storage format so that they compile in parallel
 UNITS = ["rlbm_api.cu", "rlbm_f64.cu", "rlbm_mixed.cu", "rlbm_mixed_f32.cu", "rlbm_mixed_f32dev.cu",
-         "rlbm_mixed_bf16.cu", "rlbm_mixed_f16.cu", "rlbm_noalloc.cu"]
+         "rlbm_mixed_bf16.cu", "rlbm_mixed_f16.cu", "rlbm_noalloc.cu", "rlbm_peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + CSRC, "-I" + INCLUDE]

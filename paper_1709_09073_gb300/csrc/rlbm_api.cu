@@ -18,7 +18,6 @@ using namespace rlbm;
 namespace {
 
 constexpr size_t kAlign = 256;
-constexpr int kTileX = 32, kTileY = 4;
 constexpr int kChunkPairs = 16;  // a chunk graph holds 2 * kChunkPairs steps
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -87,6 +86,7 @@ void make_layout(const rlbm_config* c, Layout& L) {
   const int lpad = (int)(16 / es);
   const int pitch_mult = (int)(128 / es);
   size_t off = 0;  // elements
+  long long foff = 0;  // cells before the domain in packed field arrays
   L.dd.resize(c->ndomains);
   L.tiles.clear();
   for (int i = 0; i < c->ndomains; ++i) {
@@ -96,9 +96,13 @@ void make_layout(const rlbm_config* c, Layout& L) {
     D.nx = d.nx;
     D.ny = d.ny;
     D.lpad = lpad;
-    D.pitch = (int)align_up((size_t)(lpad + d.nx + 1), (size_t)pitch_mult);
+    // rows hold x = -1 .. nx + 1: the two-cell pull of the lean step reads x + 2
+    // for a last pair that straddles the right edge
+    D.pitch = (int)align_up((size_t)(lpad + d.nx + 2), (size_t)pitch_mult);
     D.plane = (long long)D.pitch * (d.ny + 2);
     D.off = (long long)off;
+    D.foff = foff;
+    foff += (long long)d.nx * d.ny;
     D.bc[0] = d.bc_xlo; D.bc[1] = d.bc_xhi; D.bc[2] = d.bc_ylo; D.bc[3] = d.bc_yhi;
     D.inv_tau = 1.0 / d.tau;
     D.t_wall[0] = d.t_wall_xlo; D.t_wall[1] = d.t_wall_xhi;
@@ -113,8 +117,8 @@ void make_layout(const rlbm_config* c, Layout& L) {
     D.accel_y = d.accel_y;
     D.n_wall = d.n_wall;
     off = align_up(off + 72 * (size_t)D.plane, kAlign / es);
-    for (int y0 = 0; y0 < d.ny; y0 += kTileY)
-      for (int x0 = 0; x0 < d.nx; x0 += kTileX) L.tiles.push_back(Tile{i, x0, y0, 0});
+    for (int y0 = 0; y0 < d.ny; y0 += kTileH)
+      for (int x0 = 0; x0 < d.nx; x0 += kTileW) L.tiles.push_back(Tile{i, x0, y0, 0});
   }
   L.pop_elems = off;
   L.pop_bytes = align_up(off * es, kAlign);
@@ -159,6 +163,7 @@ struct rlbm_ctx {
   long long cells = 0;
   int grid = 0;                  // blocks of the step kernel (0 = one per tile)
   int kernel = RLBM_KERNEL_L1;   // mixed step variant (rlbm_select_kernel)
+  unsigned long long wait_ns = 0;  // TMA copy-wait limit (0: the default, rlbm_set_wait_limit)
 };
 
 namespace {
@@ -178,6 +183,8 @@ cudaError_t launch_step(rlbm_ctx* h, int from) {
   const bool tma = h->d_tmaps && h->kernel == RLBM_KERNEL_TMA;
   a.tmaps = tma ? h->d_tmaps + (size_t)from * per : nullptr;
   a.tmaps_out = tma && h->L.esize == 4 ? h->d_tmaps + (size_t)(2 + 1 - from) * per : nullptr;
+  a.variant = h->kernel;
+  a.wait_ns = h->wait_ns;
   const int grid = h->grid > 0 ? h->grid : a.ntiles;
   if (h->storage == RLBM_F64) return launch_step_f64(h->edf, a, grid, h->stream);
   return launch_step_mixed(h->storage, h->edf, a, grid, h->stream);
@@ -437,6 +444,8 @@ int rlbm_init(rlbm_handle h, int domain, int kind, const double* a, const double
   ia.a = da; ia.theta = dt; ia.ux = dx; ia.uy = dy;
   ia.f = h->pop[h->cur];
   ia.status = h->d_status;
+  ia.tiles = nullptr;
+  ia.ntiles = 0;
   if (e == cudaSuccess)
     e = h->storage == RLBM_F64 ? launch_init_f64(h->edf, ia, d.nx, d.ny, h->stream)
                                : launch_init_mixed(h->storage, h->edf, ia, d.nx, d.ny, h->stream);
@@ -491,6 +500,8 @@ int rlbm_moments(rlbm_handle h, int domain, int streamed, double* n, double* the
   const size_t cnt = (size_t)d.nx * d.ny;
   FieldsArgs fa;
   fa.diag = nullptr;
+  fa.tiles = nullptr;
+  fa.ntiles = 0;
   fa.doms = h->d_doms;
   fa.dom = domain;
   fa.streamed = streamed ? 1 : 0;
@@ -515,12 +526,97 @@ int rlbm_moments(rlbm_handle h, int domain, int streamed, double* n, double* the
   return cuda_fail(e);
 }
 
+int rlbm_init_all(rlbm_handle h, int kind, const double* a, const double* theta, const double* ux,
+                  const double* uy, int on_device) {
+  if (!h || !a || !theta || !ux || !uy) return RLBM_E_ARG;
+  if (kind != RLBM_INIT_N_THETA && kind != RLBM_INIT_Z_THETA) return RLBM_E_ARG;
+  const size_t n = (size_t)h->cells;
+  const double *da = a, *dt = theta, *dx = ux, *dy = uy;
+  cudaError_t e = cudaSuccess;
+  if (!on_device) {
+    if (4 * n > staging_doubles(h)) return RLBM_E_UNSUPPORTED;
+    double* s = staging(h);
+    e = cudaMemcpyAsync(s, a, n * 8, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s + n, theta, n * 8, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s + 2 * n, ux, n * 8, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s + 3 * n, uy, n * 8, cudaMemcpyHostToDevice, h->stream);
+    da = s; dt = s + n; dx = s + 2 * n; dy = s + 3 * n;
+  }
+  if (e != cudaSuccess) return RLBM_E_CUDA;
+  // this call's status only: read and keep the earlier bits, clear, launch,
+  // read this call's bits, put the earlier ones back
+  e = cudaMemcpyAsync(h->h_status, h->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return RLBM_E_CUDA;
+  const unsigned saved = *h->h_status;
+  e = cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), h->stream);
+  InitArgs ia;
+  ia.doms = h->d_doms;
+  ia.dom = 0;
+  ia.kind = kind;
+  ia.a = da; ia.theta = dt; ia.ux = dx; ia.uy = dy;
+  ia.f = h->pop[h->cur];
+  ia.status = h->d_status;
+  ia.tiles = h->d_tiles;
+  ia.ntiles = (int)h->L.tiles.size();
+  if (e == cudaSuccess)
+    e = h->storage == RLBM_F64 ? launch_init_f64(h->edf, ia, 0, 0, h->stream)
+                               : launch_init_mixed(h->storage, h->edf, ia, 0, 0, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->h_status, h->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return RLBM_E_CUDA;
+  const unsigned st = *h->h_status;
+  *h->h_status = saved;
+  e = cudaMemcpyAsync(h->d_status, h->h_status, sizeof(unsigned), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return RLBM_E_CUDA;
+  for (char& v : h->initialized) v = 1;
+  return (int)st;
+}
+
+int rlbm_moments_all(rlbm_handle h, int streamed, double* n, double* theta, double* ux, double* uy, double* z,
+                     int on_device) {
+  if (!h || !n || !theta || !ux || !uy) return RLBM_E_ARG;
+  for (char v : h->initialized)
+    if (!v) return RLBM_E_STATE;
+  const size_t cnt = (size_t)h->cells;
+  FieldsArgs fa;
+  fa.diag = nullptr;
+  fa.tiles = h->d_tiles;
+  fa.ntiles = (int)h->L.tiles.size();
+  fa.doms = h->d_doms;
+  fa.dom = 0;
+  fa.streamed = streamed ? 1 : 0;
+  fa.f = h->pop[h->cur];
+  fa.status = h->d_status;
+  if (on_device) {
+    fa.n = n; fa.theta = theta; fa.ux = ux; fa.uy = uy; fa.z = z;
+  } else {
+    if (5 * cnt > staging_doubles(h)) return RLBM_E_UNSUPPORTED;
+    double* s = staging(h);
+    fa.n = s; fa.theta = s + cnt; fa.ux = s + 2 * cnt; fa.uy = s + 3 * cnt; fa.z = s + 4 * cnt;
+  }
+  cudaError_t e = h->storage == RLBM_F64 ? launch_fields_f64(h->edf, fa, 0, 0, h->stream)
+                                          : launch_fields_mixed(h->storage, h->edf, fa, 0, 0, h->stream);
+  if (e == cudaSuccess && !on_device) {
+    double* outs[5] = {n, theta, ux, uy, z};
+    double* srcs[5] = {fa.n, fa.theta, fa.ux, fa.uy, fa.z};
+    for (int k = 0; k < 5 && e == cudaSuccess; ++k)
+      if (outs[k]) e = cudaMemcpyAsync(outs[k], srcs[k], cnt * 8, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  }
+  return cuda_fail(e);
+}
+
 int rlbm_diagnostics(rlbm_handle h, int domain, int streamed, double* out, int on_device) {
   if (!h || domain < 0 || domain >= h->ndom || !out) return RLBM_E_ARG;
   if (!h->initialized[domain]) return RLBM_E_STATE;
   const rlbm_domain& d = h->doms[domain];
   const size_t cnt = (size_t)d.nx * d.ny;
   FieldsArgs fa;
+  fa.tiles = nullptr;
+  fa.ntiles = 0;
   fa.doms = h->d_doms;
   fa.dom = domain;
   fa.streamed = streamed ? 1 : 0;
@@ -624,6 +720,10 @@ int rlbm_tune(rlbm_handle h, int repeats) {
   if (cudaEventCreate(&t1) != cudaSuccess) { cudaEventDestroy(t0); return RLBM_E_CUDA; }
   // kernel variants: the mixed storages with TMA descriptors have two
   std::vector<int> kernels = {RLBM_KERNEL_L1};
+  if (h->storage != RLBM_F64) {
+    kernels.push_back(RLBM_KERNEL_LEAN);
+    kernels.push_back(RLBM_KERNEL_LEAN2);
+  }
   if (h->d_tmaps) kernels.push_back(RLBM_KERNEL_TMA);
   float best = 1e30f;
   int best_grid = ntiles, best_kernel = h->kernel;
@@ -660,13 +760,28 @@ int rlbm_tune(rlbm_handle h, int repeats) {
 int rlbm_select_kernel(rlbm_handle h, int kernel) {
   if (!h) return RLBM_E_ARG;
   if (kernel < 0) return h->kernel;
-  if (kernel != RLBM_KERNEL_L1 && kernel != RLBM_KERNEL_TMA) return RLBM_E_ARG;
+  if (kernel != RLBM_KERNEL_L1 && kernel != RLBM_KERNEL_TMA && kernel != RLBM_KERNEL_LEAN &&
+      kernel != RLBM_KERNEL_LEAN2)
+    return RLBM_E_ARG;
   if (kernel == RLBM_KERNEL_TMA && !h->d_tmaps) return RLBM_E_UNSUPPORTED;
+  if ((kernel == RLBM_KERNEL_LEAN || kernel == RLBM_KERNEL_LEAN2) && h->storage == RLBM_F64)
+    return RLBM_E_UNSUPPORTED;
   if (kernel != h->kernel) {
     h->kernel = kernel;
     drop_graphs(h);
   }
   return kernel;
+}
+
+int rlbm_set_wait_limit(rlbm_handle h, double seconds) {
+  if (!h || seconds != seconds) return RLBM_E_ARG;
+  unsigned long long ns = 0;  // the default
+  if (seconds > 0.0) ns = seconds >= 1e9 ? ~0ull >> 1 : std::max(1ull, (unsigned long long)(seconds * 1e9));
+  if (ns != h->wait_ns) {
+    h->wait_ns = ns;
+    drop_graphs(h);  // the captured launches hold the old limit
+  }
+  return RLBM_OK;
 }
 
 int rlbm_sync_status(rlbm_handle h) {

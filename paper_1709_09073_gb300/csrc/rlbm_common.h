@@ -24,6 +24,7 @@ struct DomDev {
   int nx, ny, pitch, lpad;
   long long plane;        // elements per population plane
   long long off;          // element offset of plane 0 within a population copy
+  long long foff;         // offset of the domain's cells in packed [sum ny*nx] field arrays
   int bc[4];              // xlo, xhi, ylo, yhi
   int order, pad_;        // expansion order N of Eq. (10), 2..5
   double inv_tau;
@@ -46,6 +47,12 @@ struct DomDev {
   float b_s[6];             // 1 / a_s
 };
 
+// Cells of one work-list tile along x and y. Every step kernel covers one tile
+// per block and is launched with blocks of kTileW x kTileH threads (the lean
+// two-cell variant with kTileW / 2 x kTileH); the host builds the tile lists
+// (rlbm_create, rlbm_step_noalloc) from the same constants.
+constexpr int kTileW = 32, kTileH = 4;
+
 struct Tile {
   int dom, x0, y0, pad;
 };
@@ -59,7 +66,11 @@ struct StepArgs {
   unsigned* status;       // OR of per-cell status bits
   const void* tmaps;      // TMA load descriptors of fin, one per domain (kTensorMapBytes each), or null
   const void* tmaps_out;  // TMA store descriptors of fout (FP32 storages), or null
+  int variant;            // mixed step kernel (RLBM_KERNEL_*); the FP64 step has one
+  unsigned long long wait_ns;  // limit of the TMA variant's copy waits (0: kDefaultWaitNs)
 };
+
+constexpr unsigned long long kDefaultWaitNs = 1000000000ull;  // one second
 
 constexpr int kTensorMapBytes = 128;  // sizeof(CUtensorMap), 64-byte aligned in memory
 

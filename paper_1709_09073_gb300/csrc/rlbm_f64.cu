@@ -89,9 +89,9 @@ cudaError_t prepare_f64() {
 
 cudaError_t launch_step_f64(int edf, const StepArgs& a, int grid, cudaStream_t s) {
   switch (edf) {
-    case EDF_MJ: k_step_f64<EDF_MJ><<<grid, dim3(32, 4), kSmem64, s>>>(a); break;
-    case EDF_FD: k_step_f64<EDF_FD><<<grid, dim3(32, 4), kSmem64, s>>>(a); break;
-    default: k_step_f64<EDF_BE><<<grid, dim3(32, 4), kSmem64, s>>>(a); break;
+    case EDF_MJ: k_step_f64<EDF_MJ><<<grid, dim3(kTileW, kTileH), kSmem64, s>>>(a); break;
+    case EDF_FD: k_step_f64<EDF_FD><<<grid, dim3(kTileW, kTileH), kSmem64, s>>>(a); break;
+    default: k_step_f64<EDF_BE><<<grid, dim3(kTileW, kTileH), kSmem64, s>>>(a); break;
   }
   return cudaGetLastError();
 }

@@ -11,7 +11,8 @@
 
 namespace rlbm {
 
-constexpr int kThreads = 128;  // one cell per thread; blocks of 32 x 4 cells
+constexpr int kThreads = kTileW * kTileH;  // one cell per thread; blocks of one tile
+static_assert(kThreads == 128, "the shared-memory columns and launch bounds assume 128 cells per tile");
 
 __host__ __device__ constexpr int sgnd(double v) { return (v > 0.0) - (v < 0.0); }
 __host__ __device__ constexpr double dcos(int d) {
@@ -274,15 +275,31 @@ __device__ __noinline__ void write_vwall_ghosts(const DomDev& D, int x, int y, t
   }
 }
 
+// The cell (x, y) of domain `dom` a thread of an initialiser or read-out
+// launch covers: a block per tile of the work list, or a 2D grid over one domain.
+__device__ __forceinline__ void cell_of_launch(const Tile* tiles, int dom0, int& dom, int& x, int& y) {
+  if (tiles) {
+    const Tile tl = tiles[blockIdx.x];
+    dom = tl.dom;
+    x = tl.x0 + threadIdx.x;
+    y = tl.y0 + threadIdx.y;
+  } else {
+    dom = dom0;
+    x = blockIdx.x * blockDim.x + threadIdx.x;
+    y = blockIdx.y * blockDim.y + threadIdx.y;
+  }
+}
+
 // f = f^eq of the given fields (time zero, FP64 arithmetic), halo included.
 template <int EDF, class S>
 __global__ void __launch_bounds__(kThreads) k_init(InitArgs a) {
   extern __shared__ double sm[];
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-  const DomDev& D = a.doms[a.dom];
-  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+  int dom, x, y;
+  cell_of_launch(a.tiles, a.dom, dom, x, y);
+  const DomDev& D = a.doms[dom];
   if (x >= D.nx || y >= D.ny) return;
-  const long long i = (long long)y * D.nx + x;
+  const long long i = (a.tiles ? D.foff : 0) + (long long)y * D.nx + x;
   const double theta = a.theta[i], ux = a.ux[i], uy = a.uy[i];
   unsigned st = 0;
   double z, n, g[6];
@@ -330,8 +347,9 @@ template <int EDF, class S>
 __global__ void __launch_bounds__(kThreads) k_fields(FieldsArgs a) {
   extern __shared__ double sm[];
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-  const DomDev& D = a.doms[a.dom];
-  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+  int dom, x, y;
+  cell_of_launch(a.tiles, a.dom, dom, x, y);
+  const DomDev& D = a.doms[dom];
   if (x >= D.nx || y >= D.ny) return;
   const typename S::T* __restrict__ f = static_cast<const typename S::T*>(a.f) + D.off;
   const long long c = (long long)(y + 1) * D.pitch + D.lpad + x;
@@ -360,7 +378,7 @@ __global__ void __launch_bounds__(kThreads) k_fields(FieldsArgs a) {
   }
   CellState S_;
   unsigned st = cell_state<EDF>(N, T, S_);
-  const long long i = (long long)y * D.nx + x;
+  const long long i = (a.tiles ? D.foff : 0) + (long long)y * D.nx + x;
   if (st & ST_NONPHYSICAL) S_.n = S_.theta = S_.ux = S_.uy = S_.z = nan("");
   if (a.n) a.n[i] = S_.n;
   if (a.theta) a.theta[i] = S_.theta;
@@ -434,24 +452,30 @@ cudaError_t prepare_common_t() {
   return cudaFuncSetAttribute(k_fields<EDF, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem64);
 }
 
+// Grid of an initialiser or read-out launch: a block per tile, or a 2D grid
+// over one nx x ny domain.
+inline dim3 launch_grid(const Tile* tiles, int ntiles, int nx, int ny) {
+  return tiles ? dim3(ntiles) : dim3((nx + kTileW - 1) / kTileW, (ny + kTileH - 1) / kTileH);
+}
+
 template <class S>
 cudaError_t launch_init_t(int edf, const InitArgs& a, int nx, int ny, cudaStream_t s) {
-  dim3 grid((nx + 31) / 32, (ny + 3) / 4);
+  const dim3 grid = launch_grid(a.tiles, a.ntiles, nx, ny);
   switch (edf) {
-    case EDF_MJ: k_init<EDF_MJ, S><<<grid, dim3(32, 4), kSmem64, s>>>(a); break;
-    case EDF_FD: k_init<EDF_FD, S><<<grid, dim3(32, 4), kSmem64, s>>>(a); break;
-    default: k_init<EDF_BE, S><<<grid, dim3(32, 4), kSmem64, s>>>(a); break;
+    case EDF_MJ: k_init<EDF_MJ, S><<<grid, dim3(kTileW, kTileH), kSmem64, s>>>(a); break;
+    case EDF_FD: k_init<EDF_FD, S><<<grid, dim3(kTileW, kTileH), kSmem64, s>>>(a); break;
+    default: k_init<EDF_BE, S><<<grid, dim3(kTileW, kTileH), kSmem64, s>>>(a); break;
   }
   return cudaGetLastError();
 }
 
 template <class S>
 cudaError_t launch_fields_t(int edf, const FieldsArgs& a, int nx, int ny, cudaStream_t s) {
-  dim3 grid((nx + 31) / 32, (ny + 3) / 4);
+  const dim3 grid = launch_grid(a.tiles, a.ntiles, nx, ny);
   switch (edf) {
-    case EDF_MJ: k_fields<EDF_MJ, S><<<grid, dim3(32, 4), kSmem64, s>>>(a); break;
-    case EDF_FD: k_fields<EDF_FD, S><<<grid, dim3(32, 4), kSmem64, s>>>(a); break;
-    default: k_fields<EDF_BE, S><<<grid, dim3(32, 4), kSmem64, s>>>(a); break;
+    case EDF_MJ: k_fields<EDF_MJ, S><<<grid, dim3(kTileW, kTileH), kSmem64, s>>>(a); break;
+    case EDF_FD: k_fields<EDF_FD, S><<<grid, dim3(kTileW, kTileH), kSmem64, s>>>(a); break;
+    default: k_fields<EDF_BE, S><<<grid, dim3(kTileW, kTileH), kSmem64, s>>>(a); break;
   }
   return cudaGetLastError();
 }

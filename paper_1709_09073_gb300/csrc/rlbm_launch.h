@@ -7,12 +7,17 @@
 
 namespace rlbm {
 
+// Initialiser and read-out launches cover one domain (tiles == null: a 2D grid
+// over domain `dom`, fields [ny][nx]) or every domain at once (a block per
+// tile of the work list, fields packed domain after domain, DomDev::foff).
 struct InitArgs {
   const DomDev* doms;
   int dom, kind;
-  const double *a, *theta, *ux, *uy;  // device, [ny][nx]
+  const double *a, *theta, *ux, *uy;  // device, [ny][nx] or packed
   void* f;                            // population copy to initialise
   unsigned* status;
+  const Tile* tiles;                  // null: domain `dom` only
+  int ntiles;
 };
 
 struct FieldsArgs {
@@ -22,6 +27,8 @@ struct FieldsArgs {
   double *n, *theta, *ux, *uy, *z;    // device outputs, each may be null
   double* diag;                       // null, or [7][ny][nx]: q^0, q^x, q^y, pi^{x..x} orders 2-5
   unsigned* status;
+  const Tile* tiles;                  // null: domain `dom` only; else every domain, packed outputs
+  int ntiles;
 };
 
 struct CopyArgs {

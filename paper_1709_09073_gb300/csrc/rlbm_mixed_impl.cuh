@@ -364,6 +364,8 @@ __device__ void write_halo_mixed(const DomDev& D, int x, int y, typename S::T* _
   }
 }
 
+constexpr size_t kSmemF = 72 * kThreads * sizeof(float);  // the shared-memory column of a block
+
 #ifndef RLBM_MIXED_MIN_BLOCKS
 // resident 128-thread blocks per SM the register budget must allow: 4 (128 registers)
 // measured fastest on the 2048^2 FP32-deviation case, ahead of 3 (1.13x) and 5 (1.15x)
@@ -664,6 +666,7 @@ __global__ void __launch_bounds__(kThreads, RLBM_MIXED_MIN_BLOCKS) k_step_mixed_
   uint64_t* bar = reinterpret_cast<uint64_t*>(smt + kStages * TB::kBytes + 72 * kThreads * sizeof(float));
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   if (blockIdx.x >= a.ntiles) return;  // whole block
+  const unsigned long long wait_ns = a.wait_ns ? a.wait_ns : kDefaultWaitNs;
   if (tid == 0) {
 #pragma unroll
     for (int k = 0; k < kStages; ++k) mbar_init(&bar[k], 1);
@@ -706,7 +709,7 @@ __global__ void __launch_bounds__(kThreads, RLBM_MIXED_MIN_BLOCKS) k_step_mixed_
 #define RLBM_STAGED_DIR(d)                                                                      \
   {                                                                                             \
     constexpr int k_ = (d) % kStages;                                                           \
-    const bool ok_ = mbar_wait(&bar[k_], (use0 + (d) / kStages) & 1);                           \
+    const bool ok_ = mbar_wait(&bar[k_], (use0 + (d) / kStages) & 1, wait_ns);                  \
     pull_dir_staged<d, S>(cell0 + k_ * TB::kStageElems, D, pc, p2c, col, A[d], B[d]);           \
     if (__syncthreads_or(!ok_)) goto timed_out;                                                 \
     if (tid == 0) {                                                                             \
@@ -747,7 +750,8 @@ __global__ void __launch_bounds__(kThreads, RLBM_MIXED_MIN_BLOCKS) k_step_mixed_
   return;
 timed_out:
   // a copy did not land in time: report it, let the copies still in flight
-  // finish (bounded) so that none writes shared memory after exit, return
+  // finish (bounded by the default limit, whatever the limit of the waits
+  // above) so that none writes shared memory after exit, return
   if (tid == 0) {
     atomicOr(a.status, ST_TIMEOUT);
     if (kCol) bulk_wait_all();
@@ -755,6 +759,95 @@ timed_out:
     for (int k = 0; k < kStages; ++k)
       if (inflight & (1u << k)) mbar_wait(&bar[k], (issued[k] - 1) & 1);
   }
+}
+
+}  // namespace rlbm
+
+#include "rlbm_lean.cuh"
+
+namespace rlbm {
+
+// f = f^eq of the given fields in a mixed storage (time zero), halo included:
+// the collision's FP32 equilibrium deviations (dz_moments, dfeq_shell, with the
+// tables' conserved-moment defects removed) from the FP64 input fields. Its
+// rounding is that of every collision of the mixed step, and it runs on the
+// FP32 pipe (an FP64 initialiser costs as much as ten mixed steps on GB300).
+template <int EDF, class S>
+__global__ void __launch_bounds__(kThreads) k_init_mixed(InitArgs a) {
+  extern __shared__ float smi[];
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  int dom, x, y;
+  cell_of_launch(a.tiles, a.dom, dom, x, y);
+  const DomDev& D = a.doms[dom];
+  if (x >= D.nx || y >= D.ny) return;
+  const long long i = (a.tiles ? D.foff : 0) + (long long)y * D.nx + x;
+  const float theta = (float)a.theta[i], ux = (float)a.ux[i], uy = (float)a.uy[i];
+  unsigned st = 0;
+  float z, n, g[6];
+  if (a.kind == 1) {
+    z = (float)a.a[i];
+    g_allf<EDF>(z, g);
+    n = 2.0f * kPIf * theta * theta * g[1];
+  } else {
+    n = (float)a.a[i];
+    st |= (theta > 0.0f && n > 0.0f) ? solve_z_nt_f<EDF>(n, theta, z, g) : 0;
+  }
+  const float u2 = ux * ux + uy * uy;
+  const bool ok = (u2 < 1.0f) && (theta > 0.0f) && (n > 0.0f) && isfinite(z) && isfinite(u2);
+  if (!ok) st |= ST_NONPHYSICAL;
+  const float gam = ok ? 1.0f / sqrtf(1.0f - u2) : 1.0f;
+  typename S::T* __restrict__ f = static_cast<typename S::T*>(a.f) + D.off;
+  const long long c = (long long)(y + 1) * D.pitch + D.lpad + x;
+  const long long P = D.plane;
+  float* col = smi + tid;
+  if (ok) {
+    float zr[21], zi[21];
+    dz_moments<EDF>(D, g, theta, ux, uy, gam, -1.0f, -1.0f, zr, zi);
+    float d10 = 0.0f, d20 = 0.0f, d21r = 0.0f, d21i = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      d10 = fmaf(c_Ef[EDF][k], zr[k * (k + 1) / 2], d10);
+      d20 = fmaf(c_Ef[EDF][6 + k], zr[k * (k + 1) / 2], d20);
+    }
+#pragma unroll
+    for (int k = 1; k < 6; ++k) {
+      d21r = fmaf(c_Ef[EDF][12 + k], zr[k * (k + 1) / 2 + 1], d21r);
+      d21i = fmaf(c_Ef[EDF][12 + k], zi[k * (k + 1) / 2 + 1], d21i);
+    }
+    zr[1] -= d10;
+    zr[3] -= d20;
+    zr[4] -= d21r;
+    zi[4] -= d21i;
+#pragma unroll 1
+    for (int s = 0; s < 6; ++s) {
+      float fe[12];
+      dfeq_shell<EDF>(s, D.rres[s], zr, zi, fe);
+#pragma unroll
+      for (int d = 0; d < 12; ++d) {
+        const int q = 6 * d + s;
+        col[q * kThreads] = fe[d];
+        f[q * P + c] = S::encf(fe[d], D, s);
+      }
+    }
+  } else {
+    for (int q = 0; q < 72; ++q) {
+      col[q * kThreads] = __int_as_float(0x7fc00000);  // NaN
+      f[q * P + c] = S::encf(col[q * kThreads], D, q % 6);
+    }
+  }
+  write_halo_mixed<EDF, S, true>(D, x, y, f, col, ok, n, ux, uy, gam, st);
+  if (st) atomicOr(a.status, st);
+}
+
+template <class S>
+cudaError_t launch_init_mixed_t(int edf, const InitArgs& a, int nx, int ny, cudaStream_t s) {
+  const dim3 grid = launch_grid(a.tiles, a.ntiles, nx, ny);
+  switch (edf) {
+    case EDF_MJ: k_init_mixed<EDF_MJ, S><<<grid, dim3(kTileW, kTileH), kSmemF, s>>>(a); break;
+    case EDF_FD: k_init_mixed<EDF_FD, S><<<grid, dim3(kTileW, kTileH), kSmemF, s>>>(a); break;
+    default: k_init_mixed<EDF_BE, S><<<grid, dim3(kTileW, kTileH), kSmemF, s>>>(a); break;
+  }
+  return cudaGetLastError();
 }
 
 // Reference rest equilibrium of every domain (FP64), its FP32 rounding and
@@ -812,8 +905,6 @@ static const double h_be_logcoef[6] = RLBM_BE_LOGCOEF_INIT;
 static const double h_be_harm[6] = RLBM_BE_HARM_INIT;
 static const double h_g_zc[6] = RLBM_G_ZC_INIT;
 
-constexpr size_t kSmemF = 72 * kThreads * sizeof(float);
-
 template <class S, int EDF>
 static cudaError_t prepare_tma_t() {
   cudaError_t e = cudaFuncSetAttribute(k_step_mixed_tma<EDF, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -826,6 +917,9 @@ static cudaError_t prepare_tma_t() {
 template <class S>
 static cudaError_t prepare_s() {
   cudaError_t e;
+  if ((e = prepare_lean_t<S, EDF_MJ>())) return e;
+  if ((e = prepare_lean_t<S, EDF_FD>())) return e;
+  if ((e = prepare_lean_t<S, EDF_BE>())) return e;
   if ((e = prepare_tma_t<S, EDF_MJ>())) return e;
   if ((e = prepare_tma_t<S, EDF_FD>())) return e;
   if ((e = prepare_tma_t<S, EDF_BE>())) return e;
@@ -863,19 +957,21 @@ static cudaError_t upload_mixed_tables() {
 
 template <class S>
 static cudaError_t step_s(int edf, const StepArgs& a, int grid, cudaStream_t s) {
+  if (a.variant == kVariantLean || a.variant == kVariantLean2)
+    return launch_lean<S>(edf, a.variant == kVariantLean2 ? 2 : 1, a, grid, s);
   if (a.tmaps) {  // TMA-staged variant; without descriptors the pull goes through L1
     const size_t sm = tma_smem_bytes<S>();
     switch (edf) {
-      case EDF_MJ: k_step_mixed_tma<EDF_MJ, S><<<grid, dim3(32, 4), sm, s>>>(a); break;
-      case EDF_FD: k_step_mixed_tma<EDF_FD, S><<<grid, dim3(32, 4), sm, s>>>(a); break;
-      default: k_step_mixed_tma<EDF_BE, S><<<grid, dim3(32, 4), sm, s>>>(a); break;
+      case EDF_MJ: k_step_mixed_tma<EDF_MJ, S><<<grid, dim3(kTileW, kTileH), sm, s>>>(a); break;
+      case EDF_FD: k_step_mixed_tma<EDF_FD, S><<<grid, dim3(kTileW, kTileH), sm, s>>>(a); break;
+      default: k_step_mixed_tma<EDF_BE, S><<<grid, dim3(kTileW, kTileH), sm, s>>>(a); break;
     }
     return cudaGetLastError();
   }
   switch (edf) {
-    case EDF_MJ: k_step_mixed<EDF_MJ, S><<<grid, dim3(32, 4), kSmemF, s>>>(a); break;
-    case EDF_FD: k_step_mixed<EDF_FD, S><<<grid, dim3(32, 4), kSmemF, s>>>(a); break;
-    default: k_step_mixed<EDF_BE, S><<<grid, dim3(32, 4), kSmemF, s>>>(a); break;
+    case EDF_MJ: k_step_mixed<EDF_MJ, S><<<grid, dim3(kTileW, kTileH), kSmemF, s>>>(a); break;
+    case EDF_FD: k_step_mixed<EDF_FD, S><<<grid, dim3(kTileW, kTileH), kSmemF, s>>>(a); break;
+    default: k_step_mixed<EDF_BE, S><<<grid, dim3(kTileW, kTileH), kSmemF, s>>>(a); break;
   }
   return cudaGetLastError();
 }
@@ -898,7 +994,7 @@ static cudaError_t prepare_unit() {
 
 template <class S>
 constexpr MixedUnit mixed_unit() {
-  return MixedUnit{&prepare_unit<S>, &step_s<S>, &launch_init_t<S>, &launch_fields_t<S>, &launch_copy_t<S>};
+  return MixedUnit{&prepare_unit<S>, &step_s<S>, &launch_init_mixed_t<S>, &launch_fields_t<S>, &launch_copy_t<S>};
 }
 
 extern const MixedUnit kMixedF32, kMixedF32Dev, kMixedBF16, kMixedF16;

@@ -27,7 +27,6 @@ namespace {
 
 constexpr size_t kScratchBytes = RLBM_NOALLOC_SCRATCH_BYTES;
 constexpr size_t kAlignB = 256;
-constexpr int kTileW = 32, kTileH = 4;  // the tile shape the step kernel is launched with
 constexpr int kMaxDevices = 64;
 
 // The scratch array. The CUDA runtime reserves it on a device when this
@@ -72,6 +71,7 @@ int check_domain(const rlbm_domain* d, int edf) {
   }
   if (vw && !(d->n_wall > 0.0)) return RLBM_E_ARG;
   if (!(d->accel_x > -1.0 && d->accel_x < 1.0 && d->accel_y > -1.0 && d->accel_y < 1.0)) return RLBM_E_ARG;
+  if (!(d->eta_s >= 0.0) || !(d->eta_s < 1e300)) return RLBM_E_ARG;  // as rlbm_create checks it
   return RLBM_OK;
 }
 
@@ -185,6 +185,8 @@ extern "C" int rlbm_step_noalloc(const rlbm_domain* domain, int edf, int nsteps,
     a.status = d_status;
     a.tmaps = nullptr;
     a.tmaps_out = nullptr;
+    a.variant = 0;
+    a.wait_ns = 0;
     e = launch_step_f64(edf, a, P.ntiles, s);
     cur = 1 - cur;
   }

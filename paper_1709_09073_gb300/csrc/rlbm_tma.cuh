@@ -8,9 +8,14 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "rlbm_common.h"
+
 namespace rlbm {
 
-constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // one second
+constexpr unsigned long long kWaitLimitNs = kDefaultWaitNs;  // one second
+// limits below this poll with the non-suspending test_wait, so that a short
+// limit runs out on the first copy still in flight (failure-detection tests)
+constexpr unsigned long long kPollBelowNs = 1000ull;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -81,13 +86,31 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, unsigned parity) {
   return ok != 0;
 }
 
-// Wait until the phase of parity `parity` has completed; false after the limit.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
-  if (mbar_test(bar, parity)) return true;
+// Non-suspending test of the phase of parity `parity`.
+__device__ __forceinline__ bool mbar_poll(uint64_t* bar, unsigned parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait until the phase of parity `parity` has completed; false once limit_ns
+// have passed (a limit under kPollBelowNs polls without suspending).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, unsigned long long limit_ns = kWaitLimitNs) {
   const unsigned long long t0 = global_ns();
+  if (limit_ns < kPollBelowNs) {
+    for (;;) {
+      if (mbar_poll(bar, parity)) return true;
+      if (global_ns() - t0 > limit_ns) return false;
+    }
+  }
+  if (mbar_test(bar, parity)) return true;
   for (unsigned it = 1;; ++it) {
     if (mbar_test(bar, parity)) return true;
-    if ((it & 63u) == 0u && global_ns() - t0 > kWaitLimitNs) return false;
+    if ((it & 63u) == 0u && global_ns() - t0 > limit_ns) return false;
   }
 }
 

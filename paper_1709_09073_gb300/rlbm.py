@@ -23,13 +23,14 @@ RLBM_W_LANDAU_MAXITER, RLBM_W_CLAMPED_FUGACITY, RLBM_W_NONPHYSICAL, RLBM_W_ZSOLV
 RLBM_E_ARG, RLBM_E_CUDA, RLBM_E_STATE, RLBM_E_UNSUPPORTED, RLBM_E_NOBUFFER = -1, -2, -3, -4, -5
 RLBM_E_SCRATCH = -6
 RLBM_W_DEVICE_TIMEOUT = 16
-RLBM_KERNEL_L1, RLBM_KERNEL_TMA = 0, 1
+RLBM_KERNEL_L1, RLBM_KERNEL_TMA, RLBM_KERNEL_LEAN, RLBM_KERNEL_LEAN2 = 0, 1, 2, 3
 RLBM_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 EXPORTS = ["rlbm_workspace_bytes", "rlbm_create", "rlbm_init", "rlbm_step", "rlbm_moments",
            "rlbm_get_populations", "rlbm_set_populations", "rlbm_tune", "rlbm_sync_status",
            "rlbm_destroy", "rlbm_status_string", "rlbm_last_step_info", "rlbm_step_noalloc", "rlbm_diagnostics",
-           "rlbm_select_kernel", "rlbm_edge_row_bytes", "rlbm_pack_edge_rows", "rlbm_unpack_ghost_rows"]
+           "rlbm_select_kernel", "rlbm_edge_row_bytes", "rlbm_pack_edge_rows", "rlbm_unpack_ghost_rows",
+           "rlbm_pipe_peaks", "rlbm_set_wait_limit", "rlbm_init_all", "rlbm_moments_all"]
 
 
 class rlbm_domain(ctypes.Structure):
@@ -88,6 +89,10 @@ def load(path=None):
     L.rlbm_unpack_ghost_rows.argtypes = [_H, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
     L.rlbm_step_noalloc.argtypes = [ctypes.POINTER(rlbm_domain), ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint)]
+    L.rlbm_pipe_peaks.argtypes = [_D, _D, ctypes.POINTER(ctypes.c_int)]
+    L.rlbm_init_all.argtypes = [_H, ctypes.c_int] + [ctypes.c_void_p] * 4 + [ctypes.c_int]
+    L.rlbm_moments_all.argtypes = [_H, ctypes.c_int] + [ctypes.c_void_p] * 5 + [ctypes.c_int]
+    L.rlbm_set_wait_limit.argtypes = [_H, ctypes.c_double]
     _lib = L
     return L
 
@@ -156,6 +161,39 @@ class Simulation:
             ptrs = [f.ctypes.data_as(ctypes.c_void_p) for f in fields]
             on_dev = 0
         return _check(load().rlbm_init(self.h, domain, state.kind, *ptrs, on_dev))
+
+    def init_all(self, kind, a, theta, ux, uy):
+        """Initialise every domain at once from packed fields (the domains'
+        [ny][nx] arrays one after the other): host numpy or device torch."""
+        fields = [a, theta, ux, uy]
+        n = sum(d.nx * d.ny for d in self.specs)
+        if hasattr(a, "data_ptr"):
+            for f in fields:
+                if f.dtype != self.torch.float64 or not f.is_cuda or not f.is_contiguous() or f.numel() != n:
+                    raise ValueError("packed fields must be contiguous float64 CUDA tensors of %d values" % n)
+            ptrs, on_dev = [ctypes.c_void_p(f.data_ptr()) for f in fields], 1
+        else:
+            fields = [np.ascontiguousarray(f, dtype=np.float64).reshape(-1) for f in fields]
+            if any(f.size != n for f in fields):
+                raise ValueError("packed fields must hold %d values" % n)
+            ptrs, on_dev = [f.ctypes.data_as(ctypes.c_void_p) for f in fields], 0
+        return _check(load().rlbm_init_all(self.h, kind, *ptrs, on_dev))
+
+    def moments_all(self, streamed=True, out=None):
+        """n, theta, ux, uy, z of every domain, packed (see init_all): into the
+        five device tensors `out` if given, else returned as host arrays."""
+        n = sum(d.nx * d.ny for d in self.specs)
+        if out is not None:
+            for f in out:
+                if f.dtype != self.torch.float64 or not f.is_cuda or not f.is_contiguous() or f.numel() != n:
+                    raise ValueError("outputs must be contiguous float64 CUDA tensors of %d values" % n)
+            _check(load().rlbm_moments_all(self.h, 1 if streamed else 0,
+                                           *[ctypes.c_void_p(f.data_ptr()) for f in out], 1))
+            return out
+        res = [np.empty(n) for _ in range(5)]
+        _check(load().rlbm_moments_all(self.h, 1 if streamed else 0,
+                                       *[r.ctypes.data_as(ctypes.c_void_p) for r in res], 0))
+        return res
 
     def step(self, nsteps):
         return _check(load().rlbm_step(self.h, nsteps))
@@ -228,9 +266,13 @@ class Simulation:
         return _check(load().rlbm_tune(self.h, repeats))
 
     def select_kernel(self, kernel=-1):
-        """Select the mixed step variant (RLBM_KERNEL_L1 / RLBM_KERNEL_TMA) or,
+        """Select the mixed step variant (RLBM_KERNEL_L1, _TMA, _LEAN, _LEAN2) or,
         with no argument, return the one in use."""
         return _check(load().rlbm_select_kernel(self.h, kernel))
+
+    def set_wait_limit(self, seconds=0.0):
+        """Limit of the TMA-staged step's copy waits (0: the default one second)."""
+        return _check(load().rlbm_set_wait_limit(self.h, float(seconds)))
 
     def sync_status(self):
         return _check(load().rlbm_sync_status(self.h))
@@ -257,12 +299,31 @@ def step_noalloc(spec, edf, nsteps, f_in, f_out, stream=None, wait=True):
     device checkpoint f_in into f_out (torch float64 [72][ny+2][nx+2] on the
     GPU) using the library's fixed scratch array. Returns this call's warning
     bits when wait is true (the call then waits for the stream), else None."""
+    import torch
+    shape = (72, spec.ny + 2, spec.nx + 2)
+    for name, t in (("f_in", f_in), ("f_out", f_out)):
+        # the copy kernels trust the pointers: a wrong size, type or device would
+        # make them read or write outside the caller's buffer
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_cuda:
+            raise ValueError("%s must be a float64 CUDA tensor" % name)
+        if t.device.index != torch.cuda.current_device():
+            raise ValueError("%s must be on the current CUDA device" % name)
+        if tuple(t.shape) != shape or not t.is_contiguous():
+            raise ValueError("%s must be a contiguous tensor of shape %s" % (name, shape))
     dom = make_domains([spec])
     s = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
     w = ctypes.c_uint(0)
     _check(load().rlbm_step_noalloc(dom, edf, nsteps, ctypes.c_void_p(f_in.data_ptr()),
                                     ctypes.c_void_p(f_out.data_ptr()), s, ctypes.byref(w) if wait else None))
     return w.value if wait else None
+
+
+def pipe_peaks():
+    """Measured FP64 and FP32 FMA throughput of the current GPU (flop/s, FMA =
+    2) and its SM count: the compute ceilings of the roofline."""
+    f64, f32, sms = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+    _check(load().rlbm_pipe_peaks(ctypes.byref(f64), ctypes.byref(f32), ctypes.byref(sms)))
+    return {"fp64_flops": f64.value, "fp32_flops": f32.value, "sm_count": sms.value}
 
 
 def status_string(code):
@@ -273,6 +334,11 @@ def from_workload(wl, storage=RLBM_F64, **kw):
     """Create a Simulation for a workloads.Workload and initialise every domain."""
     edf = wl.domains[0].edf
     sim = Simulation(wl.domains, edf=edf, storage=storage, **kw)
+    kinds = {s.kind for s in wl.init}
+    if len(kinds) == 1:  # one call and one launch for every domain
+        packed = [np.concatenate([np.asarray(getattr(s, k), dtype=np.float64).reshape(-1) for s in wl.init])
+                  for k in ("a", "theta", "ux", "uy")]
+        return sim, sim.init_all(kinds.pop(), *packed)
     st = 0
     for i, s in enumerate(wl.init):
         st |= sim.init(i, s)

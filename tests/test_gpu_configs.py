@@ -7,10 +7,15 @@
   cell (its fugacity solve is a bisection), which sets these sizes.
 * Full-size runs in the launch configuration the benchmark times (autotuned
   grid and kernel, CUDA-graph replay), checked on samples the oracle can
-  compute one by one: the 8192 x 8192 hot spot at selected cells (the oracle
-  runs a patch around each cell whose border, zero-gradient, cannot reach the
-  centre within the steps taken) plus its conservation and mirror symmetry, and
-  the 256-domain batched Taylor-Green workload on whole small domains.
+  compute one by one: the 8192 x 8192 hot spot at selected cells after 60
+  steps, plus its mirror symmetry, and the 256-domain batched Taylor-Green
+  workload after the benchmark's 200 steps, on cells of its largest domains,
+  on both sides of domain-to-domain seams of the tile work list, on one whole
+  128^2-class domain and on its four smallest domains whole. A sampled cell's
+  oracle value comes from its light cone: the periodic initial state around it,
+  stepped with one ring of cells cropped after every step (a cell's state after
+  k steps depends only on cells within k of it, so the ring the zero-gradient
+  border has touched is always the one cropped).
 
 Bounds: n and theta relative, u normwise (max|du| / max|u|), 1e-5 for the FP32
 storages; the 16-bit formats hold the deviation to 2^-9 (BF16) and 2^-12 (FP16)
@@ -67,26 +72,40 @@ def test_fourier_twin_fd(R, orc, stname, code, tol):
         assert prof[0] < prof[-1]
 
 
-def _patch_reference(orc, spec, init, cx, cy, steps):
-    """Oracle fields at cell (cx, cy) after `steps` steps, from a patch of the
-    periodic initial state around it with zero-gradient borders: the border
-    error moves at most one cell per step, so the centre is exact when the
-    half-width exceeds the step count."""
-    h = steps + 2
+def _cone_reference(orc, spec, init, cx, cy, steps):
+    """Oracle fields (streamed) at cell (cx, cy) of a periodic domain after
+    `steps` steps, from its light cone (see the module docstring); also the
+    largest |u| of the final 3 x 3 patch."""
+    h = steps + 1
     xs = np.arange(cx - h, cx + h + 1) % spec.nx
     ys = np.arange(cy - h, cy + h + 1) % spec.ny
-    sub = lambda a: a[np.ix_(ys, xs)]
+    sub = lambda a: np.ascontiguousarray(a[np.ix_(ys, xs)])
     zg = (W.ZERO_GRADIENT,) * 4
-    pspec = W.DomainSpec(2 * h + 1, 2 * h + 1, spec.tau, spec.edf, zg)
-    pinit = W.InitialState(init.kind, sub(init.a), sub(init.theta), sub(init.ux), sub(init.uy))
-    ref, _ = oracle_fields(orc, pspec, pinit, steps)
-    return [r[h, h] for r in ref], max(np.max(np.abs(ref[2])), np.max(np.abs(ref[3])))
+    side = 2 * h + 1
+    dom = orc.domain(side, side, spec.tau, spec.edf, zg)
+    f, _, _ = orc.init(dom, init.kind, sub(init.a), sub(init.theta), sub(init.ux), sub(init.uy))
+    for _ in range(steps):
+        f, _, _ = orc.step(dom, f, None)
+        f = np.ascontiguousarray(f[:, 1:-1, 1:-1])
+        side -= 2
+        dom = orc.domain(side, side, spec.tau, spec.edf, zg)
+    ref, _ = orc.fields(dom, f, None, streamed=True)
+    return [r[1, 1] for r in ref], max(np.max(np.abs(ref[2])), np.max(np.abs(ref[3])))
+
+
+def _check_cell(label, fields, ref, umax, tol=1e-5):
+    g = [float(a) for a in fields]
+    e_n = abs(g[0] - ref[0]) / ref[0]
+    e_t = abs(g[1] - ref[1]) / ref[1]
+    e_u = max(abs(g[2] - ref[2]), abs(g[3] - ref[3])) / max(umax, 1e-300)
+    print("%s: n %.2e theta %.2e u %.2e" % (label, e_n, e_t, e_u))
+    assert max(e_n, e_t) <= tol and (e_u <= tol or umax < 1e-12), (label, e_n, e_t, e_u)
 
 
 def test_hot_spot_full_size_sampled(R, orc):
-    """8192^2 BE hot spot, FP32 deviations, autotuned launch, 20 steps."""
+    """8192^2 BE hot spot, FP32 deviations, autotuned launch, 60 steps."""
     import torch
-    steps = 20
+    steps = 60
     wl = W.hot_spot(L=8192, steps=steps)
     spec, init = wl.domains[0], wl.init[0]
     sim = R.Simulation([spec], edf=spec.edf, storage=R.RLBM_F32DEV)
@@ -97,14 +116,9 @@ def test_hot_spot_full_size_sampled(R, orc):
     assert (st & (R.RLBM_W_NONPHYSICAL | R.RLBM_W_ZSOLVE)) == 0
     n, th, ux, uy, _ = sim.moments(0, on_device=True)
     c = spec.nx // 2
-    for (x, y) in [(c, c), (c + 40, c - 25), (c - 90, c + 3), (17, 5000)]:
-        ref, umax = _patch_reference(orc, spec, init, x, y, steps)
-        g = [float(a[y, x]) for a in (n, th, ux, uy)]
-        e_n = abs(g[0] - ref[0]) / ref[0]
-        e_t = abs(g[1] - ref[1]) / ref[1]
-        e_u = max(abs(g[2] - ref[2]), abs(g[3] - ref[3])) / max(umax, 1e-300)
-        print("hot spot 8192 cell (%d, %d): n %.2e theta %.2e u %.2e" % (x, y, e_n, e_t, e_u))
-        assert max(e_n, e_t) <= 1e-5 and (e_u <= 1e-5 or umax < 1e-12), (x, y, e_n, e_t, e_u)
+    for (x, y) in [(c, c), (c + 40, c - 25), (c - 90, c + 3), (c + 31, c + 32), (17, 5000)]:
+        ref, umax = _cone_reference(orc, spec, init, x, y, steps)
+        _check_cell("hot spot 8192 cell (%d, %d)" % (x, y), [a[y, x] for a in (n, th, ux, uy)], ref, umax)
     # mirror symmetry about the centre and the diagonal (rounding-level)
     t = th.double()
     core = t[c - 300:c + 301, c - 300:c + 301]
@@ -115,9 +129,12 @@ def test_hot_spot_full_size_sampled(R, orc):
 
 
 def test_batched_taylor_green_full_size_sampled(R, orc):
-    """The 256-domain benchmark batch in FP32 deviations, autotuned launch, 50
-    steps: the four smallest domains agree with the oracle whole."""
-    steps = 50
+    """The 256-domain benchmark batch in FP32 deviations, autotuned launch,
+    after the benchmark's 200 steps: a cell of each of the two largest domains
+    at a corner of four tiles, the cells on both sides of three domain-to-domain
+    seams of the work list (the last cell of a domain and the first of the
+    next), one whole domain of about 128^2, and the four smallest domains whole."""
+    steps = 200
     wl = W.batched_taylor_green()
     sim = R.Simulation(wl.domains, edf=0, storage=R.RLBM_F32DEV)
     for i, s in enumerate(wl.init):
@@ -125,8 +142,27 @@ def test_batched_taylor_green_full_size_sampled(R, orc):
     sim.tune(1)
     sim.step(steps)
     assert sim.sync_status() == 0
-    small = sorted(range(len(wl.domains)), key=lambda i: wl.domains[i].nx * wl.domains[i].ny)[:4]
-    for i in small:
+    fields = {}
+
+    def at(i, x, y):
+        if i not in fields:
+            fields[i] = sim.moments(i)
+        return [a[y, x] for a in fields[i][:4]]
+
+    area = [d.nx * d.ny for d in wl.domains]
+    order = sorted(range(len(area)), key=lambda i: area[i])
+    for i in order[-2:]:
+        d = wl.domains[i]
+        for (x, y) in [(31, 3)]:
+            ref, umax = _cone_reference(orc, d, wl.init[i], x, y, steps)
+            _check_cell("batch domain %d (%dx%d) cell (%d, %d)" % (i, d.nx, d.ny, x, y), at(i, x, y), ref, umax)
+    for i in (0, 127, 254):
+        a, b = wl.domains[i], wl.domains[i + 1]
+        for j, (x, y) in ((i, (a.nx - 1, a.ny - 1)), (i + 1, (0, 0))):
+            ref, umax = _cone_reference(orc, wl.domains[j], wl.init[j], x, y, steps)
+            _check_cell("seam %d|%d: domain %d cell (%d, %d)" % (i, i + 1, j, x, y), at(j, x, y), ref, umax)
+    mid = min(range(len(area)), key=lambda i: abs(area[i] - 128 * 128))
+    for i in [mid] + order[:4]:
         ref, _ = oracle_fields(orc, wl.domains[i], wl.init[i], steps)
         errs = errors(sim.moments(i), ref)
         print("batched TG domain %d (%dx%d): n %.2e theta %.2e u %.2e" % (

@@ -77,3 +77,30 @@ def test_kernel_selection_rules(R):
     sim.init(0, W.random_domain_state(64, 16, 1))
     assert sim.tune(1) > 0 and sim.select_kernel() in (R.RLBM_KERNEL_L1, R.RLBM_KERNEL_TMA)
     sim.close()
+
+
+def test_copy_wait_limit_runs_out_and_the_handle_recovers(R):
+    """Failure detection without a fault: with the TMA variant's copy-wait limit
+    set to one nanosecond (polling, so the first copy still in flight runs it
+    out) a step ends early with RLBM_W_DEVICE_TIMEOUT and no other effect on the
+    context. With the default limit restored and the domain initialised again,
+    the next steps are clean and bit-identical to the L1 variant."""
+    spec = W.DomainSpec(512, 64, 0.9, 0)
+    init = W.random_domain_state(512, 64, 31, 0, u_amp=0.05)
+    ref, s_ref = _populations(R, [spec], [init], 4, R.RLBM_KERNEL_L1, 5)
+    sim = R.Simulation([spec], edf=0, storage=4)
+    sim.init(0, init)
+    assert sim.select_kernel(R.RLBM_KERNEL_TMA) == R.RLBM_KERNEL_TMA
+    sim.set_wait_limit(1e-9)
+    sim.step(1)
+    st = sim.sync_status()
+    assert st & R.RLBM_W_DEVICE_TIMEOUT, st
+    assert "timed out" in R.status_string(st)
+    sim.set_wait_limit(0)          # back to the default of one second
+    sim.init(0, init)              # the interrupted step left no valid state
+    sim.step(5)
+    st2 = sim.sync_status()
+    out = sim.get_populations(0)
+    sim.close()
+    assert st2 == s_ref == 0
+    assert np.array_equal(out, ref[0])
