@@ -379,8 +379,9 @@ def run_profile_case(args):
     L, storage = (2048, rlbm.RLBM_F32DEV) if args.profile_case == "mixed" else (1024, rlbm.RLBM_F64)
     wl = W.taylor_green(L=L, u0=0.02, tau=0.9, steps=3)
     sim, _ = rlbm.from_workload(wl, storage=storage)
-    if args.kernel != "l1":
-        sim.select_kernel(rlbm.RLBM_KERNEL_TMA)
+    if args.profile_case == "mixed":
+        sim.select_kernel({"l1": rlbm.RLBM_KERNEL_L1, "tma": rlbm.RLBM_KERNEL_TMA, "lean": rlbm.RLBM_KERNEL_LEAN,
+                           "lean2": rlbm.RLBM_KERNEL_LEAN2}[args.kernel])
     sim.step(3)
     torch.cuda.synchronize()
     t = timed_steps(sim, args.steps, torch) if args.steps > 0 else 0.0
@@ -553,7 +554,7 @@ def main():
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the hot-spot and Fourier-flow configurations")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--kernel", choices=["l1", "tma"], default="l1",
+    ap.add_argument("--kernel", choices=["l1", "tma", "lean", "lean2"], default="l1",
                     help="mixed step variant of --profile-case mixed")
     ap.add_argument("--peaks", action="store_true",
                     help="print the measured FP64/FP32 FMA throughput of the GPU and exit")

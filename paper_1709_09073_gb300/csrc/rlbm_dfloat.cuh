@@ -3,8 +3,11 @@
 // transformations TwoSum (Knuth) and TwoProduct (via FMA). GB300 executes FP64
 // at 1/64 of the FP32 rate, so the mixed-precision step keeps its few
 // precision-critical quantities (moment totals, Landau residual, gamma, n, eps)
-// in this form on the FP32 pipe. The compiler must not reassociate FP32
-// additions (nvcc does not without fast-math).
+// in this form on the FP32 pipe. Every operation is written with the
+// round-to-nearest intrinsics, which the compiler neither reassociates nor
+// contracts into an FMA with a neighbouring product: the error-free
+// transformations are exact only as written, and every kernel that inlines
+// them gets the same roundings.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -23,33 +26,33 @@ __device__ __forceinline__ df df_make(float hi, float lo) {
 
 // s + e = a + b exactly
 __device__ __forceinline__ df two_sum(float a, float b) {
-  const float s = a + b;
-  const float v = s - a;
-  const float e = (a - (s - v)) + (b - v);
+  const float s = __fadd_rn(a, b);
+  const float v = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, v)), __fsub_rn(b, v));
   return df_make(s, e);
 }
 
 // s + e = a + b exactly, requires |a| >= |b|
 __device__ __forceinline__ df quick_two_sum(float a, float b) {
-  const float s = a + b;
-  return df_make(s, b - (s - a));
+  const float s = __fadd_rn(a, b);
+  return df_make(s, __fsub_rn(b, __fsub_rn(s, a)));
 }
 
 // p + e = a * b exactly
 __device__ __forceinline__ df two_prod(float a, float b) {
-  const float p = a * b;
+  const float p = __fmul_rn(a, b);
   return df_make(p, fmaf(a, b, -p));
 }
 
 __device__ __forceinline__ df df_add(df a, df b) {
   df s = two_sum(a.hi, b.hi);
-  s.lo += a.lo + b.lo;
+  s.lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
   return quick_two_sum(s.hi, s.lo);
 }
 
 __device__ __forceinline__ df df_add(df a, float b) {
   df s = two_sum(a.hi, b);
-  s.lo += a.lo;
+  s.lo = __fadd_rn(s.lo, a.lo);
   return quick_two_sum(s.hi, s.lo);
 }
 
@@ -69,25 +72,25 @@ __device__ __forceinline__ df df_mul(df a, float b) {
 }
 
 // exact scaling by a power of two
-__device__ __forceinline__ df df_scale(df a, float pow2) { return df_make(a.hi * pow2, a.lo * pow2); }
+__device__ __forceinline__ df df_scale(df a, float pow2) { return df_make(__fmul_rn(a.hi, pow2), __fmul_rn(a.lo, pow2)); }
 
 // 1 / sqrt(a): rsqrtf seed and one Newton step evaluated in double-float
 __device__ __forceinline__ df df_rsqrt(df a) {
   const float g = rsqrtf(a.hi);
   // e = 1 - a g^2 (small), g1 = g + g e / 2
   const df ag2 = df_mul(df_mul(a, g), g);
-  const float e = (1.0f - ag2.hi) - ag2.lo;
-  return quick_two_sum(g, 0.5f * g * e);
+  const float e = __fsub_rn(__fsub_rn(1.0f, ag2.hi), ag2.lo);
+  return quick_two_sum(g, __fmul_rn(__fmul_rn(0.5f, g), e));
 }
 
 // a / b: FP32 quotient refined once with the double-float remainder
 __device__ __forceinline__ df df_div(df a, df b) {
-  const float q1 = a.hi / b.hi;
+  const float q1 = __fdiv_rn(a.hi, b.hi);
   const df r = df_sub(a, df_mul(b, q1));
-  const float q2 = r.hi / b.hi;
+  const float q2 = __fdiv_rn(r.hi, b.hi);
   return quick_two_sum(q1, q2);
 }
 
-__device__ __forceinline__ float df_to_float(df a) { return a.hi + a.lo; }
+__device__ __forceinline__ float df_to_float(df a) { return __fadd_rn(a.hi, a.lo); }
 
 }  // namespace rlbm

@@ -164,7 +164,7 @@ __device__ __forceinline__ unsigned collide_lean(const DomDev& D, int x, int y, 
     if (D.eta_s > 0.0) itau = 1.0f / (4.0f * (float)D.eta_s / theta + 0.2546f);
     float om[12];
 #pragma unroll
-    for (int d = 0; d < 12; ++d) om[d] = gf * (1.0f - ((float)dcos(d) * uxf + (float)dsin(d) * uyf)) * itau;
+    for (int d = 0; d < 12; ++d) om[d] = relax_rate(d, gf, uxf, uyf, itau);
 #pragma unroll kUnroll
     for (int s = 0; s < 6; ++s) {
       float fe[12];

@@ -91,7 +91,7 @@ __device__ void g_allf(float z, float g[6]) {
     float mp = 1.0f;
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-      g[i] = fmaf(mp, c_be_harmf[i] - c_be_logcoeff[i] * lnm, g[i]);
+      g[i] = fmaf(mp, fmaf(-c_be_logcoeff[i], lnm, c_be_harmf[i]), g[i]);
       mp *= mu;
     }
     return;
@@ -119,12 +119,13 @@ __device__ void g_allf(float z, float g[6]) {
   const float L = logf(z);
   const float eta2 = 0.822467033f, eta4 = 0.947032829f, eta6 = 0.985551091f;
   const float L2 = L * L, L3 = L2 * L, L4 = L3 * L, L5 = L4 * L, L6 = L5 * L;
+  // the inversion formula's polynomial in L, products and sums written out
   g[0] = -g[0] + L;
-  g[1] = g[1] + L2 / 2.0f + 2.0f * eta2;
-  g[2] = -g[2] + L3 / 6.0f + 2.0f * eta2 * L;
-  g[3] = g[3] + L4 / 24.0f + eta2 * L2 + 2.0f * eta4;
-  g[4] = -g[4] + L5 / 120.0f + eta2 * L3 / 3.0f + 2.0f * eta4 * L;
-  g[5] = g[5] + L6 / 720.0f + eta2 * L4 / 12.0f + eta4 * L2 + 2.0f * eta6;
+  g[1] = g[1] + fmaf(L2, 0.5f, 2.0f * eta2);
+  g[2] = -g[2] + fmaf(L3, 1.0f / 6.0f, (2.0f * eta2) * L);
+  g[3] = g[3] + fmaf(L4, 1.0f / 24.0f, fmaf(eta2, L2, 2.0f * eta4));
+  g[4] = -g[4] + fmaf(L5, 1.0f / 120.0f, fmaf(eta2 / 3.0f, L3, (2.0f * eta4) * L));
+  g[5] = g[5] + fmaf(L6, 1.0f / 720.0f, fmaf(eta2 / 12.0f, L4, fmaf(eta4, L2, 2.0f * eta6)));
 }
 
 // Fugacity from g_3^2/g_2^3 = target (Eq. 25), FP32 safeguarded Newton in mu = ln z.
@@ -204,38 +205,49 @@ __device__ int solve_z_nt_f(float n, float theta, float& z, float g[6]) {
 // brings u to ~1e-15. eps, gamma follow in double-float. T = {T00, T01, T02,
 // T11, T12, T22}.
 __device__ __forceinline__ int landau_df(const df T[6], df& ux, df& uy, df& eps, df& gamma) {
+  // every product that meets a sum is an explicit FMA (or the sum a rounded
+  // intrinsic), so each kernel that inlines this gets the same roundings
   const float E = T[0].hi, mx = T[1].hi, my = T[2].hi, pxx = T[3].hi, pxy = T[4].hi, pyy = T[5].hi;
-  const float disc = 9.0f * E * E - 8.0f * (mx * mx + my * my);
+  const float disc = fmaf(9.0f * E, E, -8.0f * fmaf(mx, mx, __fmul_rn(my, my)));
   if (!(E > 0.0f) || !(disc >= 0.0f)) return ST_NONPHYSICAL;
-  const float x = 0.25f * (3.0f * E + sqrtf(disc));
+  const float x = 0.25f * fmaf(3.0f, E, sqrtf(disc));
   float fu = mx / x, fv = my / x;
 #pragma unroll
   for (int it = 0; it < 3; ++it) {
-    const float a = E - (mx * fu + my * fv);
-    const float fx = mx - (pxx * fu + pxy * fv) - a * fu;
-    const float fy = my - (pxy * fu + pyy * fv) - a * fv;
-    const float j00 = fu * mx - pxx - a, j01 = fu * my - pxy, j10 = fv * mx - pxy, j11 = fv * my - pyy - a;
-    const float rdet = 1.0f / (j00 * j11 - j01 * j10);
-    fu += (j01 * fy - j11 * fx) * rdet;
-    fv += (j10 * fx - j00 * fy) * rdet;
+    const float a = fmaf(-mx, fu, fmaf(-my, fv, E));
+    const float fx = fmaf(-a, fu, fmaf(-pxx, fu, fmaf(-pxy, fv, mx)));
+    const float fy = fmaf(-a, fv, fmaf(-pxy, fu, fmaf(-pyy, fv, my)));
+    const float j00 = __fsub_rn(fmaf(fu, mx, -pxx), a), j01 = fmaf(fu, my, -pxy), j10 = fmaf(fv, mx, -pxy),
+                j11 = __fsub_rn(fmaf(fv, my, -pyy), a);
+    const float rdet = 1.0f / fmaf(j00, j11, -__fmul_rn(j01, j10));
+    fu = fmaf(fmaf(j01, fy, -__fmul_rn(j11, fx)), rdet, fu);
+    fv = fmaf(fmaf(j10, fx, -__fmul_rn(j00, fy)), rdet, fv);
   }
-  if (!(fu * fu + fv * fv < 1.0f)) return ST_NONPHYSICAL;
+  if (!(fmaf(fu, fu, __fmul_rn(fv, fv)) < 1.0f)) return ST_NONPHYSICAL;
   {
     const df a = df_sub(T[0], df_add(df_mul(T[1], fu), df_mul(T[2], fv)));
     const df rx = df_sub(df_sub(T[1], df_add(df_mul(T[3], fu), df_mul(T[4], fv))), df_mul(a, fu));
     const df ry = df_sub(df_sub(T[2], df_add(df_mul(T[4], fu), df_mul(T[5], fv))), df_mul(a, fv));
     const float af = a.hi;
-    const float j00 = fu * mx - pxx - af, j01 = fu * my - pxy, j10 = fv * mx - pxy, j11 = fv * my - pyy - af;
-    const float rdet = 1.0f / (j00 * j11 - j01 * j10);
+    const float j00 = __fsub_rn(fmaf(fu, mx, -pxx), af), j01 = fmaf(fu, my, -pxy), j10 = fmaf(fv, mx, -pxy),
+                j11 = __fsub_rn(fmaf(fv, my, -pyy), af);
+    const float rdet = 1.0f / fmaf(j00, j11, -__fmul_rn(j01, j10));
     const float gx = df_to_float(rx), gy = df_to_float(ry);
-    ux = two_sum(fu, (j01 * gy - j11 * gx) * rdet);
-    uy = two_sum(fv, (j10 * gx - j00 * gy) * rdet);
+    ux = two_sum(fu, __fmul_rn(fmaf(j01, gy, -__fmul_rn(j11, gx)), rdet));
+    uy = two_sum(fv, __fmul_rn(fmaf(j10, gx, -__fmul_rn(j00, gy)), rdet));
   }
   eps = df_sub(T[0], df_add(df_mul(T[1], ux), df_mul(T[2], uy)));
   const df w = df_sub(df_make(1.0f, 0.0f), df_add(df_mul(ux, ux), df_mul(uy, uy)));
   if (!(w.hi > 0.0f) || !(eps.hi > 0.0f)) return ST_NONPHYSICAL;
   gamma = df_rsqrt(w);
   return 0;
+}
+
+// Relaxation rate of direction d, gamma (1 - v_d . u) / tau (Eq. 3), with the
+// roundings written out (see landau_df).
+__device__ __forceinline__ float relax_rate(int d, float gam, float ux, float uy, float itau) {
+  const float vu = fmaf((float)dcos(d), ux, __fmul_rn((float)dsin(d), uy));
+  return __fmul_rn(__fmul_rn(gam, __fsub_rn(1.0f, vu)), itau);
 }
 
 // FP32 harmonic sums of a 12-vector (pairs d, d+6 folded first).
@@ -279,8 +291,8 @@ __device__ __forceinline__ void dfeq_shell(int s, float rres, const float zr[21]
     Rs[k] = as;
   }
   Rc[0] += rres;
-  const float t1 = Rc[0] + Rc[4], t2 = fmaf(-0.5f, Rc[4], Rc[0]), h2 = 0.5f * Rc[2];
-  const float Ec0 = t1 + Rc[2], Ec3 = t1 - Rc[2], Ec1 = t2 + h2, Ec2 = t2 - h2;
+  const float t1 = Rc[0] + Rc[4], t2 = fmaf(-0.5f, Rc[4], Rc[0]);
+  const float Ec0 = t1 + Rc[2], Ec3 = t1 - Rc[2], Ec1 = fmaf(0.5f, Rc[2], t2), Ec2 = fmaf(-0.5f, Rc[2], t2);
   const float Es1 = mul_h(Rs[2] + Rs[4]), Es2 = mul_h(Rs[2] - Rs[4]);
   const float E0 = Ec0, E1 = Ec1 + Es1, E2 = Ec2 + Es2, E3 = Ec3, E4 = Ec2 - Es2, E5 = Ec1 - Es1;
   const float Oc0 = Rc[1] + Rc[3] + Rc[5], Oc1 = mul_h(Rc[1] - Rc[5]), Oc2 = fmaf(0.5f, Rc[1] + Rc[5], -Rc[3]);
@@ -301,14 +313,15 @@ __device__ __forceinline__ void dfeq_shell(int s, float rres, const float zr[21]
 template <int EDF>
 __device__ __forceinline__ void dz_moments(const DomDev& D, const float g[6], float theta, float ux, float uy,
                                            float gam, float An1, float An2, float zr[21], float zi[21]) {
-  const float u2 = ux * ux + uy * uy;
+  // products that meet sums are explicit FMAs (see landau_df)
+  const float u2 = fmaf(ux, ux, __fmul_rn(uy, uy));
   float wr[6], wi[6];
   wr[0] = 1.0f;
   wi[0] = 0.0f;
 #pragma unroll
   for (int k = 1; k < 6; ++k) {
-    wr[k] = wr[k - 1] * ux - wi[k - 1] * uy;
-    wi[k] = wr[k - 1] * uy + wi[k - 1] * ux;
+    wr[k] = fmaf(wr[k - 1], ux, -__fmul_rn(wi[k - 1], uy));
+    wi[k] = fmaf(wr[k - 1], uy, __fmul_rn(wi[k - 1], ux));
   }
   float A = 2.0f * kPIf * theta;
 #pragma unroll
@@ -321,11 +334,15 @@ __device__ __forceinline__ void dz_moments(const DomDev& D, const float g[6], fl
     for (int k = 0; k <= n; ++k) {
       const int i = n * (n + 1) / 2 + k;
       const float P = fmaf(u2, fmaf(u2, c_pnkf[3 * i + 2], c_pnkf[3 * i + 1]), c_pnkf[3 * i + 0]);
-      const float sc = An * P;
-      zr[i] = sc * wr[k];
-      zi[i] = sc * wi[k];
+      if (k == 0) {
+        zr[i] = fmaf(An, P, -D.zref_f[n]);  // the isotropic moments as deviations from the reference
+        zi[i] = 0.0f;
+      } else {
+        const float sc = __fmul_rn(An, P);
+        zr[i] = __fmul_rn(sc, wr[k]);
+        zi[i] = __fmul_rn(sc, wi[k]);
+      }
     }
-    zr[n * (n + 1) / 2] -= D.zref_f[n];
   }
 }
 
@@ -460,7 +477,7 @@ __device__ __forceinline__ unsigned collide_mixed(const DomDev& D, int x, int y,
     if (D.eta_s > 0.0) itau = 1.0f / (4.0f * (float)D.eta_s / theta + 0.2546f);
     float om[12];
 #pragma unroll
-    for (int d = 0; d < 12; ++d) om[d] = gf * (1.0f - ((float)dcos(d) * uxf + (float)dsin(d) * uyf)) * itau;
+    for (int d = 0; d < 12; ++d) om[d] = relax_rate(d, gf, uxf, uyf, itau);
 #pragma unroll 1
     for (int s = 0; s < 6; ++s) {
       float fe[12];
