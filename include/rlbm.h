@@ -225,6 +225,12 @@ int rlbm_unpack_ghost_rows(rlbm_handle h, int domain, const void *lo, const void
  * warnings raised while timing are discarded. */
 int rlbm_tune(rlbm_handle h, int repeats);
 
+/* Launch the step kernel with `grid` blocks in later rlbm_step calls: a
+ * persistent grid, each block walking the tile list with stride `grid`, or
+ * one block per 32 x 4 tile for grid = 0 (the default). rlbm_tune sets it as
+ * well. Returns the grid now in use (grid >= 0) or RLBM_E_ARG. */
+int rlbm_set_grid(rlbm_handle h, int grid);
+
 /* Variants of the mixed-precision step kernel; all compute the same update
  * with the same arithmetic in the same order (identical results).
  *  RLBM_KERNEL_L1    each thread pulls its bilinear neighbours from global
@@ -239,17 +245,23 @@ int rlbm_tune(rlbm_handle h, int repeats);
  *                    the halo work confined to edge tiles and cells;
  *  RLBM_KERNEL_LEAN2 the same with two adjacent cells of a row per thread,
  *                    each plane row read by one aligned pair load and one
- *                    single load. */
+ *                    single load;
+ *  RLBM_KERNEL_STAGED the whole pull neighbourhood of a tile staged in shared
+ *                    memory by TMA (12 boxes on one barrier), the populations
+ *                    pulled into registers, and the next tile's boxes loading
+ *                    while the tile collides (persistent grids). Needs the TMA
+ *                    descriptors, as RLBM_KERNEL_TMA. */
 #define RLBM_KERNEL_L1 0
 #define RLBM_KERNEL_TMA 1
 #define RLBM_KERNEL_LEAN 2
 #define RLBM_KERNEL_LEAN2 3
+#define RLBM_KERNEL_STAGED 4
 
 /* Select the step kernel variant (kernel >= 0) or query it (kernel < 0).
  * Returns the variant now in use, RLBM_E_ARG for an unknown variant, or
- * RLBM_E_UNSUPPORTED for RLBM_KERNEL_TMA, _LEAN or _LEAN2 on FP64 storage (it
- * has one step kernel) or RLBM_KERNEL_TMA without TMA descriptors. rlbm_tune
- * may change the selection. */
+ * RLBM_E_UNSUPPORTED for a mixed variant on FP64 storage (it has one step
+ * kernel) or RLBM_KERNEL_TMA / _STAGED without TMA descriptors. rlbm_tune may
+ * change the selection. */
 int rlbm_select_kernel(rlbm_handle h, int kernel);
 
 /* Time limit of every wait of the TMA-staged step (RLBM_KERNEL_TMA) for a

@@ -181,7 +181,8 @@ cudaError_t launch_step(rlbm_ctx* h, int from) {
   // descriptors [kind][copy][domain]: loads of copy `from`, stores into the other copy
   const size_t per = (size_t)h->ndom * kTensorMapBytes;
   const bool tma = h->d_tmaps && h->kernel == RLBM_KERNEL_TMA;
-  a.tmaps = tma ? h->d_tmaps + (size_t)from * per : nullptr;
+  const bool staged = h->d_tmaps && h->kernel == RLBM_KERNEL_STAGED;
+  a.tmaps = tma || staged ? h->d_tmaps + (size_t)from * per : nullptr;
   a.tmaps_out = tma && h->L.esize == 4 ? h->d_tmaps + (size_t)(2 + 1 - from) * per : nullptr;
   a.variant = h->kernel;
   a.wait_ns = h->wait_ns;
@@ -724,7 +725,10 @@ int rlbm_tune(rlbm_handle h, int repeats) {
     kernels.push_back(RLBM_KERNEL_LEAN);
     kernels.push_back(RLBM_KERNEL_LEAN2);
   }
-  if (h->d_tmaps) kernels.push_back(RLBM_KERNEL_TMA);
+  if (h->d_tmaps) {
+    kernels.push_back(RLBM_KERNEL_TMA);
+    kernels.push_back(RLBM_KERNEL_STAGED);
+  }
   float best = 1e30f;
   int best_grid = ntiles, best_kernel = h->kernel;
   for (int kv : kernels)
@@ -757,13 +761,22 @@ int rlbm_tune(rlbm_handle h, int repeats) {
   return e == cudaSuccess ? best_grid : RLBM_E_CUDA;
 }
 
+int rlbm_set_grid(rlbm_handle h, int grid) {
+  if (!h || grid < 0) return RLBM_E_ARG;
+  if (grid != h->grid) {
+    h->grid = grid;
+    drop_graphs(h);  // the captured launches hold the old grid
+  }
+  return grid;
+}
+
 int rlbm_select_kernel(rlbm_handle h, int kernel) {
   if (!h) return RLBM_E_ARG;
   if (kernel < 0) return h->kernel;
   if (kernel != RLBM_KERNEL_L1 && kernel != RLBM_KERNEL_TMA && kernel != RLBM_KERNEL_LEAN &&
-      kernel != RLBM_KERNEL_LEAN2)
+      kernel != RLBM_KERNEL_LEAN2 && kernel != RLBM_KERNEL_STAGED)
     return RLBM_E_ARG;
-  if (kernel == RLBM_KERNEL_TMA && !h->d_tmaps) return RLBM_E_UNSUPPORTED;
+  if ((kernel == RLBM_KERNEL_TMA || kernel == RLBM_KERNEL_STAGED) && !h->d_tmaps) return RLBM_E_UNSUPPORTED;
   if ((kernel == RLBM_KERNEL_LEAN || kernel == RLBM_KERNEL_LEAN2) && h->storage == RLBM_F64)
     return RLBM_E_UNSUPPORTED;
   if (kernel != h->kernel) {

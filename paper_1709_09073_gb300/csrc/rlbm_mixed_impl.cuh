@@ -781,6 +781,7 @@ timed_out:
 }  // namespace rlbm
 
 #include "rlbm_lean.cuh"
+#include "rlbm_staged.cuh"
 
 namespace rlbm {
 
@@ -934,6 +935,9 @@ static cudaError_t prepare_tma_t() {
 template <class S>
 static cudaError_t prepare_s() {
   cudaError_t e;
+  if ((e = prepare_staged_t<S, EDF_MJ>())) return e;
+  if ((e = prepare_staged_t<S, EDF_FD>())) return e;
+  if ((e = prepare_staged_t<S, EDF_BE>())) return e;
   if ((e = prepare_lean_t<S, EDF_MJ>())) return e;
   if ((e = prepare_lean_t<S, EDF_FD>())) return e;
   if ((e = prepare_lean_t<S, EDF_BE>())) return e;
@@ -976,6 +980,7 @@ template <class S>
 static cudaError_t step_s(int edf, const StepArgs& a, int grid, cudaStream_t s) {
   if (a.variant == kVariantLean || a.variant == kVariantLean2)
     return launch_lean<S>(edf, a.variant == kVariantLean2 ? 2 : 1, a, grid, s);
+  if (a.variant == kVariantStaged) return a.tmaps ? launch_staged<S>(edf, a, grid, s) : cudaErrorInvalidValue;
   if (a.tmaps) {  // TMA-staged variant; without descriptors the pull goes through L1
     const size_t sm = tma_smem_bytes<S>();
     switch (edf) {

@@ -23,14 +23,14 @@ RLBM_W_LANDAU_MAXITER, RLBM_W_CLAMPED_FUGACITY, RLBM_W_NONPHYSICAL, RLBM_W_ZSOLV
 RLBM_E_ARG, RLBM_E_CUDA, RLBM_E_STATE, RLBM_E_UNSUPPORTED, RLBM_E_NOBUFFER = -1, -2, -3, -4, -5
 RLBM_E_SCRATCH = -6
 RLBM_W_DEVICE_TIMEOUT = 16
-RLBM_KERNEL_L1, RLBM_KERNEL_TMA, RLBM_KERNEL_LEAN, RLBM_KERNEL_LEAN2 = 0, 1, 2, 3
+RLBM_KERNEL_L1, RLBM_KERNEL_TMA, RLBM_KERNEL_LEAN, RLBM_KERNEL_LEAN2, RLBM_KERNEL_STAGED = 0, 1, 2, 3, 4
 RLBM_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 EXPORTS = ["rlbm_workspace_bytes", "rlbm_create", "rlbm_init", "rlbm_step", "rlbm_moments",
            "rlbm_get_populations", "rlbm_set_populations", "rlbm_tune", "rlbm_sync_status",
            "rlbm_destroy", "rlbm_status_string", "rlbm_last_step_info", "rlbm_step_noalloc", "rlbm_diagnostics",
            "rlbm_select_kernel", "rlbm_edge_row_bytes", "rlbm_pack_edge_rows", "rlbm_unpack_ghost_rows",
-           "rlbm_pipe_peaks", "rlbm_set_wait_limit", "rlbm_init_all", "rlbm_moments_all"]
+           "rlbm_pipe_peaks", "rlbm_set_wait_limit", "rlbm_init_all", "rlbm_moments_all", "rlbm_set_grid"]
 
 
 class rlbm_domain(ctypes.Structure):
@@ -93,6 +93,7 @@ def load(path=None):
     L.rlbm_init_all.argtypes = [_H, ctypes.c_int] + [ctypes.c_void_p] * 4 + [ctypes.c_int]
     L.rlbm_moments_all.argtypes = [_H, ctypes.c_int] + [ctypes.c_void_p] * 5 + [ctypes.c_int]
     L.rlbm_set_wait_limit.argtypes = [_H, ctypes.c_double]
+    L.rlbm_set_grid.argtypes = [_H, ctypes.c_int]
     _lib = L
     return L
 
@@ -266,9 +267,13 @@ class Simulation:
         return _check(load().rlbm_tune(self.h, repeats))
 
     def select_kernel(self, kernel=-1):
-        """Select the mixed step variant (RLBM_KERNEL_L1, _TMA, _LEAN, _LEAN2) or,
+        """Select the mixed step variant (RLBM_KERNEL_L1, _TMA, _LEAN, _LEAN2, _STAGED) or,
         with no argument, return the one in use."""
         return _check(load().rlbm_select_kernel(self.h, kernel))
+
+    def set_grid(self, grid=0):
+        """Persistent grid of `grid` blocks for the step kernel (0: one block per tile)."""
+        return _check(load().rlbm_set_grid(self.h, int(grid)))
 
     def set_wait_limit(self, seconds=0.0):
         """Limit of the TMA-staged step's copy waits (0: the default one second)."""
