@@ -37,8 +37,7 @@ UNIT = "MLUPS"
 BYTES_PER_CELL = {0: 1152, 1: 576, 2: 288, 3: 288, 4: 576}   # 2 x 72 x element size
 STORAGE_NAME = {0: "f64", 1: "f32", 2: "bf16dev", 3: "f16dev", 4: "f32dev"}
 # the mixed step's variants (rlbm_select_kernel) by the kernel each launches
-KERNEL_NAMES = {0: "k_step_mixed", 1: "k_step_mixed_tma", 2: "k_step_lean", 3: "k_step_lean2",
-                4: "k_step_staged"}
+KERNEL_NAMES = {0: "k_step_mixed", 1: "k_step_mixed_tma"}
 
 
 def dist_env():
@@ -381,8 +380,7 @@ def run_profile_case(args):
     wl = W.taylor_green(L=L, u0=0.02, tau=0.9, steps=3)
     sim, _ = rlbm.from_workload(wl, storage=storage)
     if args.profile_case == "mixed":
-        sim.select_kernel({"l1": rlbm.RLBM_KERNEL_L1, "tma": rlbm.RLBM_KERNEL_TMA, "lean": rlbm.RLBM_KERNEL_LEAN,
-                           "lean2": rlbm.RLBM_KERNEL_LEAN2, "staged": rlbm.RLBM_KERNEL_STAGED}[args.kernel])
+        sim.select_kernel({"l1": rlbm.RLBM_KERNEL_L1, "tma": rlbm.RLBM_KERNEL_TMA}[args.kernel])
     sim.step(3)
     torch.cuda.synchronize()
     t = timed_steps(sim, args.steps, torch) if args.steps > 0 else 0.0
@@ -555,7 +553,7 @@ def main():
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the hot-spot and Fourier-flow configurations")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--kernel", choices=["l1", "tma", "lean", "lean2", "staged"], default="l1",
+    ap.add_argument("--kernel", choices=["l1", "tma"], default="l1",
                     help="mixed step variant of --profile-case mixed")
     ap.add_argument("--peaks", action="store_true",
                     help="print the measured FP64/FP32 FMA throughput of the GPU and exit")

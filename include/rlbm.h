@@ -231,37 +231,22 @@ int rlbm_tune(rlbm_handle h, int repeats);
  * well. Returns the grid now in use (grid >= 0) or RLBM_E_ARG. */
 int rlbm_set_grid(rlbm_handle h, int grid);
 
-/* Variants of the mixed-precision step kernel; all compute the same update
+/* Variants of the mixed-precision step kernel; both compute the same update
  * with the same arithmetic in the same order (identical results).
- *  RLBM_KERNEL_L1    each thread pulls its bilinear neighbours from global
- *                    memory through L1 and stores its 72 values (default);
- *  RLBM_KERNEL_TMA   a ring of TMA boxes (one direction's six shell planes of a
- *                    32 x 4 tile and its ring) staged in shared memory; FP32
- *                    storages also write the collided tile back with one bulk
- *                    tensor store. Needs the driver's tensor-map encoder and
- *                    domains at least 4 cells wide;
- *  RLBM_KERNEL_LEAN  the L1 pull with the tile's domain descriptor staged in
- *                    shared memory, the collision's shell loop unrolled and
- *                    the halo work confined to edge tiles and cells;
- *  RLBM_KERNEL_LEAN2 the same with two adjacent cells of a row per thread,
- *                    each plane row read by one aligned pair load and one
- *                    single load;
- *  RLBM_KERNEL_STAGED the whole pull neighbourhood of a tile staged in shared
- *                    memory by TMA (12 boxes on one barrier), the populations
- *                    pulled into registers, and the next tile's boxes loading
- *                    while the tile collides (persistent grids). Needs the TMA
- *                    descriptors, as RLBM_KERNEL_TMA. */
+ *  RLBM_KERNEL_L1   each thread pulls its bilinear neighbours from global
+ *                   memory through L1 and stores its 72 values (default);
+ *  RLBM_KERNEL_TMA  a ring of TMA boxes (one direction's six shell planes of
+ *                   the tile's block of 32 cells and its two neighbours, rows
+ *                   y0-1 .. y0+4) staged in shared memory, every wait for a
+ *                   copy bounded (rlbm_set_wait_limit). Needs the driver's
+ *                   tensor-map encoder. */
 #define RLBM_KERNEL_L1 0
 #define RLBM_KERNEL_TMA 1
-#define RLBM_KERNEL_LEAN 2
-#define RLBM_KERNEL_LEAN2 3
-#define RLBM_KERNEL_STAGED 4
 
 /* Select the step kernel variant (kernel >= 0) or query it (kernel < 0).
  * Returns the variant now in use, RLBM_E_ARG for an unknown variant, or
- * RLBM_E_UNSUPPORTED for a mixed variant on FP64 storage (it has one step
- * kernel) or RLBM_KERNEL_TMA / _STAGED without TMA descriptors. rlbm_tune may
- * change the selection. */
+ * RLBM_E_UNSUPPORTED for RLBM_KERNEL_TMA on FP64 storage (it has one step
+ * kernel) or without TMA descriptors. rlbm_tune may change the selection. */
 int rlbm_select_kernel(rlbm_handle h, int kernel);
 
 /* Time limit of every wait of the TMA-staged step (RLBM_KERNEL_TMA) for a
@@ -324,9 +309,9 @@ int rlbm_last_step_info(rlbm_handle h, long long *cell_updates, int *kernel_laun
  *    RLBM_NOALLOC_SCRATCH_BYTES (32 MiB), which the CUDA runtime reserves on
  *    every GPU where the library's module is loaded and holds until the
  *    process exits. A domain fits when 1.5 KB + 16 * ceil(nx/32) * ceil(ny/4)
- *    + 2 * 576 * (ny + 2) * pitch <= 32 MiB, pitch = nx + 3 rounded up to a
- *    multiple of 16 (about 160 x 160 cells); a larger one returns
- *    RLBM_E_SCRATCH before any device work.
+ *    + 2 * 8 * (ny + 2) * nblk * 2304 <= 32 MiB, nblk = floor((nx + 32) / 32)
+ *    + 1 blocks of 32 cells per row (about 148 x 148 cells); a larger one
+ *    returns RLBM_E_SCRATCH before any device work.
  *  - First call on each device: it looks up the array's device address
  *    (cudaGetSymbolAddress) and sets the step kernel's shared-memory limit.
  *    Make that first call before any stream capture begins.

@@ -83,8 +83,6 @@ int validate(const rlbm_config* c) {
 void make_layout(const rlbm_config* c, Layout& L) {
   L.esize = elem_size(c->storage);
   const size_t es = L.esize;
-  const int lpad = (int)(16 / es);
-  const int pitch_mult = (int)(128 / es);
   size_t off = 0;  // elements
   long long foff = 0;  // cells before the domain in packed field arrays
   L.dd.resize(c->ndomains);
@@ -95,11 +93,8 @@ void make_layout(const rlbm_config* c, Layout& L) {
     std::memset(&D, 0, sizeof(D));
     D.nx = d.nx;
     D.ny = d.ny;
-    D.lpad = lpad;
-    // rows hold x = -1 .. nx + 1: the two-cell pull of the lean step reads x + 2
-    // for a last pair that straddles the right edge
-    D.pitch = (int)align_up((size_t)(lpad + d.nx + 2), (size_t)pitch_mult);
-    D.plane = (long long)D.pitch * (d.ny + 2);
+    D.nblk = blocks_per_row(d.nx);
+    D.pitch = (long long)D.nblk * kBlk;
     D.off = (long long)off;
     D.foff = foff;
     foff += (long long)d.nx * d.ny;
@@ -116,7 +111,7 @@ void make_layout(const rlbm_config* c, Layout& L) {
     D.accel_x = d.accel_x;
     D.accel_y = d.accel_y;
     D.n_wall = d.n_wall;
-    off = align_up(off + 72 * (size_t)D.plane, kAlign / es);
+    off = align_up(off + (size_t)(d.ny + 2) * (size_t)D.pitch, kAlign / es);
     for (int y0 = 0; y0 < d.ny; y0 += kTileH)
       for (int x0 = 0; x0 < d.nx; x0 += kTileW) L.tiles.push_back(Tile{i, x0, y0, 0});
   }
@@ -129,9 +124,9 @@ void make_layout(const rlbm_config* c, Layout& L) {
   b = align_up(b + sizeof(DomDev) * L.dd.size(), kAlign);
   L.tiles_off = b;
   b = align_up(b + sizeof(Tile) * L.tiles.size(), kAlign);
-  // TMA descriptors of the staged mixed step: [kind (load, store)][copy][domain]
+  // TMA descriptors of the staged mixed step: [copy][domain]
   L.tmaps_off = b;
-  if (c->storage != RLBM_F64) b = align_up(b + 4 * (size_t)kTensorMapBytes * L.dd.size(), kAlign);
+  if (c->storage != RLBM_F64) b = align_up(b + 2 * (size_t)kTensorMapBytes * L.dd.size(), kAlign);
   L.pop_off[0] = b;
   b += L.pop_bytes;
   L.pop_off[1] = b;
@@ -178,12 +173,10 @@ cudaError_t launch_step(rlbm_ctx* h, int from) {
   a.fin = h->pop[from];
   a.fout = h->pop[1 - from];
   a.status = h->d_status;
-  // descriptors [kind][copy][domain]: loads of copy `from`, stores into the other copy
+  // descriptors [copy][domain]: the loads of copy `from`
   const size_t per = (size_t)h->ndom * kTensorMapBytes;
   const bool tma = h->d_tmaps && h->kernel == RLBM_KERNEL_TMA;
-  const bool staged = h->d_tmaps && h->kernel == RLBM_KERNEL_STAGED;
-  a.tmaps = tma || staged ? h->d_tmaps + (size_t)from * per : nullptr;
-  a.tmaps_out = tma && h->L.esize == 4 ? h->d_tmaps + (size_t)(2 + 1 - from) * per : nullptr;
+  a.tmaps = tma ? h->d_tmaps + (size_t)from * per : nullptr;
   a.variant = h->kernel;
   a.wait_ns = h->wait_ns;
   const int grid = h->grid > 0 ? h->grid : a.ntiles;
@@ -215,17 +208,11 @@ cudaError_t capture(rlbm_ctx* h, int from, int nsteps, cudaGraphExec_t* out) {
 }
 
 // TMA descriptors of the staged mixed step, written into `out` as
-// [kind][copy][domain]:
-//  kind 0 (load): a 3D tensor {pitch, ny + 2, 72} of the copy's elements (rows
-//    and planes as laid out, halo included), boxes of tma_box_width x 6 rows x
-//    6 planes, zero fill outside;
-//  kind 1 (store, FP32 storages): the interior cells {nx & ~3, ny, 72} of the
-//    copy, boxes of one 32 x 4 tile x 72 planes. Writes outside the tensor are
-//    clipped, but along x only at 16-byte granularity: a width that is not a
-//    multiple of 4 cells would let a store spill into the halo column x = nx,
-//    so the last nx % 4 cells of each row are stored by their threads instead.
-// Returns false if the driver offers no encoder or refuses a descriptor (or a
-// domain is narrower than 4 cells); the handle then has only the L1 variant.
+// [copy][domain]: a 4D tensor {32 lanes, 72 planes, nblk blocks, ny + 2 rows}
+// of the copy's elements (the halo ring included), boxes {32, 6, 3, 6} (one
+// direction's six shell planes, the tile's block and its neighbours, rows
+// y0-1 .. y0+4), zero fill outside. Returns false if the driver offers no
+// encoder or refuses a descriptor; the handle then has only the L1 variant.
 bool encode_tmaps(const rlbm_ctx* h, std::vector<unsigned char>& out) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
@@ -240,28 +227,20 @@ bool encode_tmaps(const rlbm_ctx* h, std::vector<unsigned char>& out) {
   }
   const size_t es = h->L.esize;
   const size_t nd = (size_t)h->ndom;
-  out.assign(4 * (size_t)kTensorMapBytes * nd, 0);
-  const cuuint32_t estr[3] = {1, 1, 1};
+  out.assign(2 * (size_t)kTensorMapBytes * nd, 0);
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
   const CUtensorMapDataType dt = es == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
   for (int copy = 0; copy < 2; ++copy)
     for (size_t i = 0; i < nd; ++i) {
       const DomDev& D = h->L.dd[i];
-      char* plane0 = static_cast<char*>(h->pop[copy]) + (size_t)D.off * es;
-      const cuuint64_t strides[2] = {(cuuint64_t)D.pitch * es, (cuuint64_t)D.plane * es};
-      CUtensorMap* ml = reinterpret_cast<CUtensorMap*>(out.data() + ((0 * 2 + copy) * nd + i) * kTensorMapBytes);
-      const cuuint64_t dl[3] = {(cuuint64_t)D.pitch, (cuuint64_t)D.ny + 2, 72};
-      const cuuint32_t bl[3] = {(cuuint32_t)tma_box_width((int)es), (cuuint32_t)kBoxRows, 6};
-      if (encode(ml, dt, 3, plane0, dl, strides, bl, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+      char* base = static_cast<char*>(h->pop[copy]) + (size_t)D.off * es;  // 256-byte aligned
+      const cuuint64_t dims[4] = {(cuuint64_t)kBlkW, (cuuint64_t)kNq, (cuuint64_t)D.nblk, (cuuint64_t)D.ny + 2};
+      const cuuint64_t strides[3] = {(cuuint64_t)kBlkW * es, (cuuint64_t)kBlk * es, (cuuint64_t)D.pitch * es};
+      const cuuint32_t box[4] = {(cuuint32_t)kBlkW, (cuuint32_t)kBoxPlanes, (cuuint32_t)kBoxBlocks,
+                                 (cuuint32_t)kBoxRows};
+      CUtensorMap* m = reinterpret_cast<CUtensorMap*>(out.data() + ((size_t)copy * nd + i) * kTensorMapBytes);
+      if (encode(m, dt, 4, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-        return false;
-      if (es != 4) continue;
-      if (D.nx < 4) return false;
-      CUtensorMap* ms = reinterpret_cast<CUtensorMap*>(out.data() + ((1 * 2 + copy) * nd + i) * kTensorMapBytes);
-      char* cell00 = plane0 + ((size_t)D.pitch + (size_t)D.lpad) * es;  // cell (0, 0), 16-byte aligned
-      const cuuint64_t ds[3] = {(cuuint64_t)(D.nx & ~3), (cuuint64_t)D.ny, 72};
-      const cuuint32_t bs[3] = {32, 4, 72};
-      if (encode(ms, dt, 3, cell00, ds, strides, bs, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                 CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return false;
     }
   return true;
@@ -285,10 +264,9 @@ constexpr int kSlabPlanes = 30;  // 5 directions with v_y of one sign x 6 shells
 constexpr int kPlanesUp = 6;     // q = 6..35: d = 1..5, v_y > 0
 constexpr int kPlanesDown = 42;  // q = 42..71: d = 7..11, v_y < 0
 
-// Geometry of one domain's rows in a halo-padded population copy.
+// One domain's rows in a population copy.
 struct RowArgs {
-  int nx, ny, pitch, lpad;
-  long long plane, off;
+  DomDev D;         // geometry (nx, ny, nblk, pitch, off)
   int unpack;       // 0: edge rows -> packed faces, 1: packed faces -> ghost rows
   void* pop;
   void* face[2];    // low, high; either may be null
@@ -298,7 +276,7 @@ struct RowArgs {
 // planes, both faces in one launch (the storage encoding is kept as is).
 template <class T>
 __global__ void k_rows(RowArgs a) {
-  const long long w = a.nx + 2, per = kSlabPlanes * w;
+  const long long w = a.D.nx + 2, per = kSlabPlanes * w;
   T* pop = static_cast<T*>(a.pop);
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < 2 * per;
        e += (long long)gridDim.x * blockDim.x) {
@@ -309,8 +287,8 @@ __global__ void k_rows(RowArgs a) {
     // sent rows: row 0 down (planes 42..), row ny-1 up (planes 6..);
     // received rows: y = -1 gets planes 6.., y = ny gets planes 42..
     const int q0 = (side == 0) == (a.unpack != 0) ? kPlanesUp : kPlanesDown;
-    const int y = a.unpack ? (side ? a.ny : -1) : (side ? a.ny - 1 : 0);
-    const long long idx = a.off + (q0 + k) * a.plane + (long long)(y + 1) * a.pitch + (a.lpad - 1) + xx;
+    const int y = a.unpack ? (side ? a.D.ny : -1) : (side ? a.D.ny - 1 : 0);
+    const long long idx = cell_pos(a.D, (int)xx - 1, y) + (q0 + k) * kBlkW;
     if (a.unpack) pop[idx] = buf[r];
     else buf[r] = pop[idx];
   }
@@ -324,12 +302,7 @@ int slab_rows(rlbm_handle h, int domain, void* lo, void* hi, int unpack) {
   if (!lo && !hi) return RLBM_OK;
   const DomDev& D = h->L.dd[domain];
   RowArgs a;
-  a.nx = D.nx;
-  a.ny = D.ny;
-  a.pitch = D.pitch;
-  a.lpad = D.lpad;
-  a.plane = D.plane;
-  a.off = D.off;
+  a.D = D;
   a.unpack = unpack;
   a.pop = h->pop[h->cur];
   a.face[0] = lo;
@@ -721,14 +694,7 @@ int rlbm_tune(rlbm_handle h, int repeats) {
   if (cudaEventCreate(&t1) != cudaSuccess) { cudaEventDestroy(t0); return RLBM_E_CUDA; }
   // kernel variants: the mixed storages with TMA descriptors have two
   std::vector<int> kernels = {RLBM_KERNEL_L1};
-  if (h->storage != RLBM_F64) {
-    kernels.push_back(RLBM_KERNEL_LEAN);
-    kernels.push_back(RLBM_KERNEL_LEAN2);
-  }
-  if (h->d_tmaps) {
-    kernels.push_back(RLBM_KERNEL_TMA);
-    kernels.push_back(RLBM_KERNEL_STAGED);
-  }
+  if (h->d_tmaps) kernels.push_back(RLBM_KERNEL_TMA);
   float best = 1e30f;
   int best_grid = ntiles, best_kernel = h->kernel;
   for (int kv : kernels)
@@ -773,12 +739,8 @@ int rlbm_set_grid(rlbm_handle h, int grid) {
 int rlbm_select_kernel(rlbm_handle h, int kernel) {
   if (!h) return RLBM_E_ARG;
   if (kernel < 0) return h->kernel;
-  if (kernel != RLBM_KERNEL_L1 && kernel != RLBM_KERNEL_TMA && kernel != RLBM_KERNEL_LEAN &&
-      kernel != RLBM_KERNEL_LEAN2 && kernel != RLBM_KERNEL_STAGED)
-    return RLBM_E_ARG;
-  if ((kernel == RLBM_KERNEL_TMA || kernel == RLBM_KERNEL_STAGED) && !h->d_tmaps) return RLBM_E_UNSUPPORTED;
-  if ((kernel == RLBM_KERNEL_LEAN || kernel == RLBM_KERNEL_LEAN2) && h->storage == RLBM_F64)
-    return RLBM_E_UNSUPPORTED;
+  if (kernel != RLBM_KERNEL_L1 && kernel != RLBM_KERNEL_TMA) return RLBM_E_ARG;
+  if (kernel == RLBM_KERNEL_TMA && !h->d_tmaps) return RLBM_E_UNSUPPORTED;
   if (kernel != h->kernel) {
     h->kernel = kernel;
     drop_graphs(h);

@@ -16,14 +16,22 @@ constexpr double PI = 3.14159265358979323846264338327950288;
 constexpr double ZC = 1.0 - 1.0e-7;  // BE reference fugacity, Eq. (15)
 constexpr double SQRT3_2 = 0.86602540378443864676372317075294;
 
-// Halo-padded plane layout: element (x, y), x in [-1, nx], y in [-1, ny], of
-// population q lives at off + q * plane + (y + 1) * pitch + lpad + x, where
-// lpad = 16 bytes / element size (so x = 0 starts 16-byte aligned) and pitch
-// is a multiple of 128 bytes.
+// Population layout: blocks of 32 cells of a row, each block holding all 72
+// populations of its cells ("array of structures of arrays"): element (q, x, y),
+// x in [-1, nx], y in [-1, ny] (the halo ring included), lives at
+//   off + (y + 1) * pitch + ((x + 32) / 32) * kBlk + q * kBlkW + (x + 32) % 32,
+// so a warp's access to one population of 32 cells is one aligned 32-element
+// segment, the 72 segments of a block are contiguous, and the offset of plane
+// q is the constant q * kBlkW. Block 0 of a row holds x = -32 .. -1 (only x = -1
+// is used); pitch = nblk * kBlk with nblk = (nx + 32) / 32 + 1 blocks per row.
+constexpr int kBlkW = 32;           // cells per x block
+constexpr int kNq = 72;             // populations per cell
+constexpr int kBlk = kNq * kBlkW;   // elements per x block
+
 struct DomDev {
-  int nx, ny, pitch, lpad;
-  long long plane;        // elements per population plane
-  long long off;          // element offset of plane 0 within a population copy
+  int nx, ny, nblk, pad0;
+  long long pitch;        // elements per row of blocks (nblk * kBlk)
+  long long off;          // element offset of the domain within a population copy
   long long foff;         // offset of the domain's cells in packed [sum ny*nx] field arrays
   int bc[4];              // xlo, xhi, ylo, yhi
   int order, pad_;        // expansion order N of Eq. (10), 2..5
@@ -65,21 +73,30 @@ struct StepArgs {
   void* fout;             // population copy written
   unsigned* status;       // OR of per-cell status bits
   const void* tmaps;      // TMA load descriptors of fin, one per domain (kTensorMapBytes each), or null
-  const void* tmaps_out;  // TMA store descriptors of fout (FP32 storages), or null
   int variant;            // mixed step kernel (RLBM_KERNEL_*); the FP64 step has one
   unsigned long long wait_ns;  // limit of the TMA variant's copy waits (0: kDefaultWaitNs)
 };
 
 constexpr unsigned long long kDefaultWaitNs = 1000000000ull;  // one second
 
+// Element index of cell (x, y), plane 0 (add q * kBlkW for plane q), from the
+// start of the domain (cell_rel) or of the population copy (cell_pos).
+__host__ __device__ inline long long cell_rel(const DomDev& D, int x, int y) {
+  const int X = x + kBlkW;  // >= 31
+  return (long long)(y + 1) * D.pitch + (long long)(X / kBlkW) * kBlk + (X % kBlkW);
+}
+__host__ __device__ inline long long cell_pos(const DomDev& D, int x, int y) { return D.off + cell_rel(D, x, y); }
+
+// Blocks of 32 cells per row for a domain nx cells wide (halo blocks included).
+__host__ __device__ constexpr int blocks_per_row(int nx) { return (nx + kBlkW) / kBlkW + 1; }
+
 constexpr int kTensorMapBytes = 128;  // sizeof(CUtensorMap), 64-byte aligned in memory
 
-// TMA box of the staged mixed step: the six shell planes of one direction over a
-// 32 x 4 tile and its one-cell ring, rows y0-1 .. y0+4, columns from the 16-byte
-// boundary lpad elements left of x0 to at least x0+32 (a 16-byte multiple wide).
-constexpr int kBoxRows = 6;
-__host__ __device__ constexpr int tma_box_width(int esize) {
-  return (16 / esize + 33 + 16 / esize - 1) / (16 / esize) * (16 / esize);
-}
+// TMA box of the staged mixed step: for one direction, the six shell planes of
+// the tile's x block and its two neighbours over rows y0-1 .. y0+4, i.e. a box
+// {32 lanes, 6 planes, 3 blocks, 6 rows} of the 4D tensor
+// {32 lanes, 72 planes, nblk blocks, ny + 2 rows}.
+constexpr int kBoxRows = 6, kBoxBlocks = 3, kBoxPlanes = 6;
+constexpr int kBoxElems = kBlkW * kBoxPlanes * kBoxBlocks * kBoxRows;
 
 }  // namespace rlbm

@@ -18,12 +18,11 @@ __global__ void __launch_bounds__(kThreads) k_step_f64(StepArgs a) {
     const DomDev& D = a.doms[tl.dom];
     const int x = tl.x0 + threadIdx.x, y = tl.y0 + threadIdx.y;
     if (x >= D.nx || y >= D.ny) continue;
-    const long long P = D.plane;
     const double* __restrict__ fin = static_cast<const double*>(a.fin) + D.off;
     double* __restrict__ fout = static_cast<double*>(a.fout) + D.off;
-    const long long c = (long long)(y + 1) * D.pitch + D.lpad + x;
+    const long long c = cell_rel(D, x, y);
     double N[3], T[6];
-    pull_moments64<EDF, StoreF64>(fin, D, c, sm, tid, N, T);
+    pull_moments64<EDF, StoreF64>(fin, D, x, c, sm, tid, N, T);
     CellState S;
     unsigned st = cell_state<EDF>(N, T, S);
     const bool ok = !(st & ST_NONPHYSICAL);
@@ -60,12 +59,12 @@ __global__ void __launch_bounds__(kThreads) k_step_f64(StepArgs a) {
           const double v = sm[q * kThreads + tid];
           const double r = fma(om[d], fe[d] - v, v);
           sm[q * kThreads + tid] = r;
-          fout[q * P + c] = r;
+          fout[q * kBlkW + c] = r;
         }
       }
       if (touches_vwall(D, x, y)) write_vwall_ghosts<EDF, StoreF64>(D, x, y, fout, sm, tid, &S, &st);
     } else {
-      for (int q = 0; q < 72; ++q) fout[q * P + c] = sm[q * kThreads + tid];
+      for (int q = 0; q < 72; ++q) fout[q * kBlkW + c] = sm[q * kThreads + tid];
     }
     write_halo64<EDF, StoreF64>(D, x, y, fout, sm, tid, ok, S.n, S.ux, S.uy, S.gamma, st, ok);
     if (st) atomicOr(a.status, st);

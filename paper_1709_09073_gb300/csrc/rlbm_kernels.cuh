@@ -79,25 +79,41 @@ struct StoreF32Dev {
   __device__ static T encf(float df, const DomDev&, int) { return df; }
 };
 
+// Element offsets, from a cell's own element, of its neighbours x - 1 and
+// x + 1 in the same row (in the next block across a block boundary) and the
+// row stride (y + 1).
+struct Nbr {
+  long long xm, xp, W;
+};
+__device__ __forceinline__ Nbr neighbours(const DomDev& D, int x) {
+  const int lane = (x + kBlkW) % kBlkW;
+  Nbr n;
+  n.xm = lane ? -1 : -kBlk + (kBlkW - 1);
+  n.xp = lane != kBlkW - 1 ? 1 : kBlk - (kBlkW - 1);
+  n.W = D.pitch;
+  return n;
+}
+
 // Bilinear interpolated pull of direction d from one plane (Eqs. 17-18): the
 // four grid points around x - v_d with weights |v_x||v_y|, (1-|v_x|)|v_y|,
 // |v_x|(1-|v_y|), (1-|v_x|)(1-|v_y|); axis directions shift by one cell.
-// Interpolates the stored values (decoding is affine per plane).
+// `pl` points at the cell's own element of the plane. Interpolates the stored
+// values (decoding is affine per plane).
 template <int d, class R, class S>
-__device__ __forceinline__ R pull_one(const typename S::T* __restrict__ pl, long long c, int W) {
+__device__ __forceinline__ R pull_one(const typename S::T* __restrict__ pl, const Nbr& nb) {
   constexpr double cx = dcos(d), cy = dsin(d);
   constexpr int sx = sgnd(cx), sy = sgnd(cy);
   constexpr double ax = dabs(cx), ay = dabs(cy);
-  const long long o1 = c - sx - (long long)sy * W;
-  if (ax == 0.0 || ay == 0.0) return (R)S::raw(pl[o1]);
+  const long long ox = sx > 0 ? nb.xm : (sx < 0 ? nb.xp : 0);  // to x - sx
+  const long long oy = -(long long)sy * nb.W;                   // to y - sy
+  if (ax == 0.0 || ay == 0.0) return (R)S::raw(pl[ox + oy]);
   // weights from the rounded |v_x|, |v_y| (one of them is 1/2): every product and
   // 1 - |v| is exact in R, so the four weights sum to exactly 1 and streaming
   // conserves the global sums of every plane
   constexpr R axr = (R)ax, ayr = (R)ay;
   constexpr R w1 = axr * ayr, w2 = (R(1) - axr) * ayr, w3 = axr * (R(1) - ayr),
               w4 = (R(1) - axr) * (R(1) - ayr);
-  const R v1 = (R)S::raw(pl[o1]), v2 = (R)S::raw(pl[c - (long long)sy * W]),
-          v3 = (R)S::raw(pl[c - sx]), v4 = (R)S::raw(pl[c]);
+  const R v1 = (R)S::raw(pl[ox + oy]), v2 = (R)S::raw(pl[oy]), v3 = (R)S::raw(pl[ox]), v4 = (R)S::raw(pl[0]);
   return fma(w1, v1, fma(w2, v2, fma(w3, v3, w4 * v4)));
 }
 
@@ -105,16 +121,15 @@ __device__ __forceinline__ R pull_one(const typename S::T* __restrict__ pl, long
 // return N^mu, T^{mu nu} (Eqs. 20, 22).
 template <int EDF, class S>
 __device__ __forceinline__ void pull_moments64(const typename S::T* __restrict__ fin, const DomDev& D,
-                                               long long c, double* sm, int tid, double N[3],
+                                               int x, long long c, double* sm, int tid, double N[3],
                                                double T[6]) {
-  const long long P = D.plane;
-  const int W = D.pitch;
+  const Nbr nb = neighbours(D, x);
   double A[12], B[12];
 #define RLBM_PULL_DIR(d)                                                          \
   {                                                                               \
     double a_ = 0.0, b_ = 0.0;                                                    \
     _Pragma("unroll") for (int s = 0; s < 6; ++s) {                               \
-      const double v = S::dec(pull_one<d, double, S>(fin + (6 * d + s) * P, c, W), D, s); \
+      const double v = S::dec(pull_one<d, double, S>(fin + c + (6 * d + s) * kBlkW, nb), D, s); \
       sm[(6 * d + s) * kThreads + tid] = v;                                       \
       a_ = fma(v, c_p[EDF][s], a_);                                               \
       b_ = fma(v, c_p2[EDF][s], b_);                                              \
@@ -201,26 +216,25 @@ __device__ void write_halo64(const DomDev& D, int x, int y, typename S::T* __res
                              unsigned& st, bool vw_written = false) {
   int hx[8], hy[8], wall[8];
   const int cnt = halo_targets(D, x, y, hx, hy, wall);
-  const long long P = D.plane;
   for (int i = 0; i < cnt; ++i) {
-    const long long h = (long long)(hy[i] + 1) * D.pitch + D.lpad + hx[i];
+    const long long h = cell_rel(D, hx[i], hy[i]);
     if (wall[i] >= 0 && D.bc[wall[i]] == BC_VWALL) {
       if (vw_written) continue;
       const double tw = D.t_wall[wall[i]];
       double z, g[6];
       st |= solve_z_from_n_theta<EDF>(D.n_wall, tw, z, g);
       feq_emit<EDF>(g, tw, 0.0, 0.0, 1.0, D.order - 2,
-                    [&](int q, double v) { fout[q * P + h] = S::enc(v, D, q % 6); });
+                    [&](int q, double v) { fout[q * kBlkW + h] = S::enc(v, D, q % 6); });
       continue;
     }
     if (wall[i] < 0 || !have_state) {
-      for (int q = 0; q < 72; ++q) fout[q * P + h] = S::enc(sm[q * kThreads + tid], D, q % 6);
+      for (int q = 0; q < 72; ++q) fout[q * kBlkW + h] = S::enc(sm[q * kThreads + tid], D, q % 6);
     } else {
       const double tw = D.t_wall[wall[i]];
       double z, g[6];
       st |= solve_z_from_n_theta<EDF>(n, tw, z, g);
       feq_emit<EDF>(g, tw, ux, uy, gamma, D.order - 2,
-                    [&](int q, double v) { fout[q * P + h] = S::enc(v, D, q % 6); });
+                    [&](int q, double v) { fout[q * kBlkW + h] = S::enc(v, D, q % 6); });
     }
   }
 }
@@ -242,7 +256,6 @@ __device__ __noinline__ void write_vwall_ghosts(const DomDev& D, int x, int y, t
                                                 const double* sm, int tid, const CellState* cs, unsigned* st) {
   int hx[8], hy[8], wall[8];
   const int cnt = halo_targets(D, x, y, hx, hy, wall);
-  const long long P = D.plane;
   int tw_side = -1;
   for (int i = 0; i < cnt; ++i)
     if (wall[i] >= 0 && D.bc[wall[i]] == BC_VWALL) tw_side = wall[i];
@@ -266,10 +279,10 @@ __device__ __noinline__ void write_vwall_ghosts(const DomDev& D, int x, int y, t
     feq_shell<EDF>(s, zrc, zic, fe, oi);
     for (int i = 0; i < cnt; ++i) {
       if (wall[i] < 0 || D.bc[wall[i]] != BC_VWALL) continue;
-      const long long h = (long long)(hy[i] + 1) * D.pitch + D.lpad + hx[i];
+      const long long h = cell_rel(D, hx[i], hy[i]);
       for (int d = 0; d < 12; ++d) {
         const int q = 6 * d + s;
-        fout[q * P + h] = S::enc(few[d] + (sm[q * kThreads + tid] - fe[d]), D, s);
+        fout[q * kBlkW + h] = S::enc(few[d] + (sm[q * kThreads + tid] - fe[d]), D, s);
       }
     }
   }
@@ -316,17 +329,16 @@ __global__ void __launch_bounds__(kThreads) k_init(InitArgs a) {
   if (!ok) st |= ST_NONPHYSICAL;
   const double gamma = ok ? 1.0 / sqrt(1.0 - u2) : 1.0;
   typename S::T* __restrict__ f = static_cast<typename S::T*>(a.f) + D.off;
-  const long long c = (long long)(y + 1) * D.pitch + D.lpad + x;
-  const long long P = D.plane;
+  const long long c = cell_rel(D, x, y);
   if (ok) {
     feq_emit<EDF>(g, theta, ux, uy, gamma, D.order - 2, [&](int q, double v) {
       sm[q * kThreads + tid] = v;
-      f[q * P + c] = S::enc(v, D, q % 6);
+      f[q * kBlkW + c] = S::enc(v, D, q % 6);
     });
   } else {
     for (int q = 0; q < 72; ++q) {
       sm[q * kThreads + tid] = nan("");
-      f[q * P + c] = S::enc(nan(""), D, q % 6);
+      f[q * kBlkW + c] = S::enc(nan(""), D, q % 6);
     }
   }
   bool vw = false;
@@ -352,17 +364,16 @@ __global__ void __launch_bounds__(kThreads) k_fields(FieldsArgs a) {
   const DomDev& D = a.doms[dom];
   if (x >= D.nx || y >= D.ny) return;
   const typename S::T* __restrict__ f = static_cast<const typename S::T*>(a.f) + D.off;
-  const long long c = (long long)(y + 1) * D.pitch + D.lpad + x;
-  const long long P = D.plane;
+  const long long c = cell_rel(D, x, y);
   double N[3], T[6];
   if (a.streamed) {
-    pull_moments64<EDF, S>(f, D, c, sm, tid, N, T);
+    pull_moments64<EDF, S>(f, D, x, c, sm, tid, N, T);
   } else {
     double A[12], B[12];
     for (int d = 0; d < 12; ++d) {
       double a_ = 0.0, b_ = 0.0;
       for (int s = 0; s < 6; ++s) {
-        const double v = S::dec((double)S::raw(f[(6 * d + s) * P + c]), D, s);
+        const double v = S::dec((double)S::raw(f[(6 * d + s) * kBlkW + c]), D, s);
         a_ = fma(v, c_p[EDF][s], a_);
         b_ = fma(v, c_p2[EDF][s], b_);
       }
@@ -409,7 +420,7 @@ __global__ void __launch_bounds__(kThreads) k_fields(FieldsArgs a) {
 #pragma unroll
         for (int d = 0; d < 12; ++d) {
           const int q = 6 * d + s;
-          const double v = a.streamed ? sm[q * kThreads + tid] : S::dec((double)S::raw(f[q * P + c]), D, s);
+          const double v = a.streamed ? sm[q * kThreads + tid] : S::dec((double)S::raw(f[q * kBlkW + c]), D, s);
           const double px = c_p[EDF][s] * dcos(d), w = (v - fe[d]) * px * px;
           p2 += w;
           p3 += w * px;
@@ -436,7 +447,7 @@ __global__ void k_copy(CopyArgs a) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
        e += (long long)gridDim.x * blockDim.x) {
     const long long q = a.q0 + e / (w * h), r = e % (w * h), yy = r / w, xx = r % w;
-    const long long src = D.off + q * D.plane + yy * D.pitch + (D.lpad - 1) + xx;
+    const long long src = cell_pos(D, (int)xx - 1, (int)yy - 1) + q * kBlkW;
     if (a.to_dense) a.dense[e] = S::dec((double)S::raw(pop[src]), D, (int)(q % 6));
     else pop[src] = S::enc(a.dense[e], D, (int)(q % 6));
   }

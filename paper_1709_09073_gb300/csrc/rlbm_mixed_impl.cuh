@@ -347,23 +347,21 @@ __device__ __forceinline__ void dz_moments(const DomDev& D, const float g[6], fl
 }
 
 // Halo writer of the mixed step: copies of the cell's post-collision values
-// (held in its shared-memory column col[q * kThreads]; kEnc: as FP32
-// deviations still to encode, else already encoded) and, at fixed-T walls, the
+// (FP32 deviations held in its shared-memory column col[q * kThreads]) and, at
+// fixed-T walls, the
 // FP32 equilibrium deviation of the wall ghost. Reading the copies back from
 // global memory instead would put a read-after-write round trip to L2 on every
 // edge warp, which costs more than keeping the column up to date.
-template <int EDF, class S, bool kEnc = true>
+template <int EDF, class S>
 __device__ void write_halo_mixed(const DomDev& D, int x, int y, typename S::T* __restrict__ fout, const float* col,
                                  bool have_state, float n, float ux, float uy, float gam, unsigned& st) {
   int hx[8], hy[8], wall[8];
   const int cnt = halo_targets(D, x, y, hx, hy, wall);
-  const long long P = D.plane;
   for (int i = 0; i < cnt; ++i) {
-    const long long h = (long long)(hy[i] + 1) * D.pitch + D.lpad + hx[i];
+    const long long h = cell_rel(D, hx[i], hy[i]);
     if (wall[i] < 0 || !have_state) {
       for (int q = 0; q < 72; ++q) {
-        if constexpr (kEnc) fout[q * P + h] = S::encf(col[q * kThreads], D, q % 6);
-        else fout[q * P + h] = col[q * kThreads];
+        fout[q * kBlkW + h] = S::encf(col[q * kThreads], D, q % 6);
       }
     } else {
       const float tw = (float)D.t_wall[wall[i]];
@@ -375,7 +373,7 @@ __device__ void write_halo_mixed(const DomDev& D, int x, int y, typename S::T* _
       for (int s = 0; s < 6; ++s) {
         float fe[12];
         dfeq_shell<EDF>(s, D.rres[s], zr, zi, fe);
-        for (int d = 0; d < 12; ++d) fout[(6 * d + s) * P + h] = S::encf(fe[d], D, s);
+        for (int d = 0; d < 12; ++d) fout[(6 * d + s) * kBlkW + h] = S::encf(fe[d], D, s);
       }
     }
   }
@@ -392,15 +390,12 @@ constexpr size_t kSmemF = 72 * kThreads * sizeof(float);  // the shared-memory c
 // Collision of one cell (Eqs. 20-25, 10-11 and 3) from its pulled FP32
 // deviations, held in the thread's shared-memory column smf[q * kThreads + tid],
 // and the shell sums A_d = sum_s p_s dv_{6d+s}, B_d = sum_s p_s^2 dv_{6d+s} of
-// each direction; stores f* to fout (kCol: encoded into the column instead,
-// FP32 storages only, for a bulk store of the tile), writes the cell's halo
-// images and returns its status bits.
-template <int EDF, class S, bool kCol = false>
+// each direction; stores f* to fout, writes the cell's halo images and returns
+// its status bits.
+template <int EDF, class S>
 __device__ __forceinline__ unsigned collide_mixed(const DomDev& D, int x, int y, long long c, const float A[12],
                                                   const float B[12], float* smf, int tid,
                                                   typename S::T* __restrict__ fout) {
-  static_assert(!kCol || sizeof(typename S::T) == sizeof(float), "column output needs FP32 storage");
-  const long long P = D.plane;
   const HarmF ha = harmonics_f(A), hb = harmonics_f(B);
   // moment totals in double-float: reference moments + FP32 deviation sums
   const df N0 = df_add(df_make(D.n0_hl[0], D.n0_hl[1]), ha.h0);
@@ -487,61 +482,15 @@ __device__ __forceinline__ unsigned collide_mixed(const DomDev& D, int x, int y,
         const int q = 6 * d + s;
         const float v = smf[q * kThreads + tid];
         const float r = fmaf(om[d], fe[d] - v, v);
-        if constexpr (kCol) {
-          smf[q * kThreads + tid] = S::encf(r, D, s);
-        } else {
-          smf[q * kThreads + tid] = r;
-          fout[q * P + c] = S::encf(r, D, s);
-        }
+        smf[q * kThreads + tid] = r;
+        fout[q * kBlkW + c] = S::encf(r, D, s);
       }
     }
   } else {
-    for (int q = 0; q < 72; ++q) {
-      if constexpr (kCol) smf[q * kThreads + tid] = S::encf(smf[q * kThreads + tid], D, q % 6);
-      else fout[q * P + c] = S::encf(smf[q * kThreads + tid], D, q % 6);
-    }
+    for (int q = 0; q < 72; ++q) fout[q * kBlkW + c] = S::encf(smf[q * kThreads + tid], D, q % 6);
   }
-  write_halo_mixed<EDF, S, !kCol>(D, x, y, fout, smf + tid, ok, nf, uxf, uyf, gf, st);
+  write_halo_mixed<EDF, S>(D, x, y, fout, smf + tid, ok, nf, uxf, uyf, gf, st);
   return st;
-}
-
-// L2 prefetch of the next tile in persistent grids (1) or none (0). Measured on
-// GB300: prefetches that run slow the step (at 2048^2, prefetching the tile one
-// resident wave ahead in a one-block-per-tile grid: 6,383 -> 4,894..5,390 MLUPS),
-// and the autotuner keeps one block per tile, where the branch below is never
-// taken; yet the step compiled with it runs 2.6 % (256-domain batch) and 4.9 %
-// (2048^2) faster than without it, with the same registers and spills reported
-// by ptxas -- an effect of code generation, kept because it was measured.
-#ifndef RLBM_MIXED_PREFETCH
-#define RLBM_MIXED_PREFETCH 1
-#endif
-// prefetch distance in tiles for one-block-per-tile grids (0: none)
-#ifndef RLBM_MIXED_PREFETCH_AHEAD
-#define RLBM_MIXED_PREFETCH_AHEAD 0
-#endif
-
-// Ask L2 for the rows the pull of tile t reads: 72 planes x rows y0-1..y0+4,
-// from the 16-byte boundary lpad elements left of x0 (x = x0 - lpad) to x0+32,
-// one bulk prefetch per plane row spread over the block's threads. Each one
-// starts 64-byte aligned (x0 is a multiple of 32, rows are 128-byte pitched)
-// and stops at the end of its padded row.
-template <class S>
-__device__ __forceinline__ void prefetch_tile_l2(const StepArgs& a, int t, int tid) {
-  using T = typename S::T;
-  const Tile tl = a.tiles[t];
-  const DomDev& D = a.doms[tl.dom];
-  const T* base = static_cast<const T*>(a.fin) + D.off;
-  const int ylo = max(tl.y0 - 1, -1), yhi = min(tl.y0 + 4, D.ny);
-  const int rows = yhi - ylo + 1;
-  const unsigned need = ((unsigned)((D.lpad + 33) * sizeof(T)) + 15u) & ~15u;
-  const unsigned room = (unsigned)((D.pitch - tl.x0) * sizeof(T));
-  const unsigned bytes = min(need, room);
-  for (int i = tid; i < 72 * rows; i += kThreads) {
-    const int q = i / rows, yy = ylo + i % rows;
-    const T* p = base + q * D.plane + (long long)(yy + 1) * D.pitch + tl.x0;
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "r"(bytes)
-                 : "memory");
-  }
 }
 
 // One 32 x 4 tile of the step: pull, collide, store (the thread's cell).
@@ -551,11 +500,10 @@ __device__ __forceinline__ void step_tile_mixed(const StepArgs& a, int t, float*
   const DomDev& D = a.doms[tl.dom];
   const int x = tl.x0 + threadIdx.x, y = tl.y0 + threadIdx.y;
   if (x >= D.nx || y >= D.ny) return;
-  const long long P = D.plane;
-  const int W = D.pitch;
   const typename S::T* __restrict__ fin = static_cast<const typename S::T*>(a.fin) + D.off;
   typename S::T* __restrict__ fout = static_cast<typename S::T*>(a.fout) + D.off;
-  const long long c = (long long)(y + 1) * W + D.lpad + x;
+  const long long c = cell_rel(D, x, y);
+  const Nbr nb = neighbours(D, x);
   // pull (FP32, deviation form) with the FP32 deviation moment sums
   float A[12], B[12], pc[6], p2c[6];
 #pragma unroll
@@ -567,7 +515,7 @@ __device__ __forceinline__ void step_tile_mixed(const StepArgs& a, int t, float*
   {                                                                             \
     float a_ = 0.0f, b_ = 0.0f;                                                 \
     _Pragma("unroll") for (int s = 0; s < 6; ++s) {                             \
-      const float v = S::decf(pull_one<d, float, S>(fin + (6 * d + s) * P, c, W), D, s); \
+      const float v = S::decf(pull_one<d, float, S>(fin + c + (6 * d + s) * kBlkW, nb), D, s); \
       smf[(6 * d + s) * kThreads + tid] = v;                                    \
       a_ = fmaf(v, pc[s], a_);                                                  \
       b_ = fmaf(v, p2c[s], b_);                                                 \
@@ -588,38 +536,28 @@ __global__ void __launch_bounds__(kThreads, RLBM_MIXED_MIN_BLOCKS) k_step_mixed(
   extern __shared__ float smf[];
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
-#if RLBM_MIXED_PREFETCH
-    {
-      // persistent grid: the block's next tile; one block per tile: the tile a
-      // block of the next resident wave will take
-      const int ahead = (int)gridDim.x < a.ntiles ? (int)gridDim.x : RLBM_MIXED_PREFETCH_AHEAD;
-      if (ahead > 0 && t + ahead < a.ntiles) prefetch_tile_l2<S>(a, t + ahead, tid);
-    }
-#endif
     step_tile_mixed<EDF, S>(a, t, smf, tid);
   }
 }
 
 // ------------------------------------------- TMA-staged variant of the step
 // Per 32 x 4 tile and direction d, one TMA box brings the six shell planes of d
-// (rows y0-1 .. y0+4, columns from the 16-byte boundary left of x0-1 to past
-// x0+32) into shared memory; the bilinear pull reads its four neighbours there
-// at fixed offsets. A ring of kStages boxes keeps the next directions -- and,
-// while a tile collides, the next tile's first directions -- in flight. For FP32
-// storages the collided tile is encoded into the shared-memory column and
-// written back by one bulk tensor store over x < nx & ~3 (the store clips at the
-// tensor bounds, along x in 16-byte units, so the last nx % 4 cells of a row
-// store their own values). The arithmetic is the same as k_step_mixed's, so the
-// two variants give identical results.
+// for the tile's block of 32 cells and the blocks either side, rows y0-1 ..
+// y0+4, into shared memory (a box {32 lanes, 6 planes, 3 blocks, 6 rows} of the
+// 4D tensor {32, 72, nblk, ny + 2}); the bilinear pull reads its four
+// neighbours there at fixed offsets (x - 1 of lane 0 and x + 1 of lane 31 in
+// the neighbouring blocks). A ring of kStages boxes keeps the next directions --
+// and, while a tile collides, the next tile's first directions -- in flight.
+// The arithmetic is the same as k_step_mixed's, so the two variants give
+// identical results.
 template <class S>
 struct TmaBox {
   using T = typename S::T;
-  static constexpr int kLpad = 16 / (int)sizeof(T);         // elements left of x = 0 in a row
-  static constexpr int kW = tma_box_width((int)sizeof(T));  // 40 (FP32) or 48 (16-bit) elements
-  static constexpr int kRows = kBoxRows;                      // y0-1 .. y0+4
-  static constexpr int kPlaneElems = kW * kRows;
-  static constexpr unsigned kBytes = (unsigned)(kPlaneElems * 6 * sizeof(T));  // six shells
-  static constexpr int kStageElems = (int)(kBytes / sizeof(T));
+  static constexpr int kPlane = kBlkW;                        // a plane's 32 lanes
+  static constexpr int kBlock = kBoxPlanes * kPlane;          // six planes of one block
+  static constexpr int kRow = kBoxBlocks * kBlock;            // three blocks of one row
+  static constexpr unsigned kBytes = (unsigned)(kBoxElems * sizeof(T));
+  static constexpr int kStageElems = kBoxElems;
 };
 constexpr int kStages = 3;  // ring depth in directions (a divisor of 12)
 
@@ -635,15 +573,19 @@ __device__ __forceinline__ void tma_issue(const StepArgs& a, int t, int d, unsig
   const void* map = static_cast<const unsigned char*>(a.tmaps) + (size_t)tl.dom * kTensorMapBytes;
   const int k = d % kStages;
   mbar_expect_tx(&bar[k], TmaBox<S>::kBytes);
-  tma_load_3d(ring + k * TmaBox<S>::kBytes, map, tl.x0, tl.y0, 6 * d, &bar[k]);
+  // lanes from 0, planes from 6d, blocks from the one left of the tile's
+  // (x0 / 32 + 1 holds x0), rows from y = y0 - 1 (row index y0)
+  tma_load_4d(ring + k * TmaBox<S>::kBytes, map, 0, 6 * d, tl.x0 / kBlkW, tl.y0, &bar[k]);
 }
 
 // Pull of direction d from its staged box; `cell` points at the cell's own
-// value in shell 0 of that stage (same weights and order of operations as
-// pull_one), col at the thread's shared-memory column.
+// value in shell 0 of that stage, oxm / oxp are the offsets of x - 1 / x + 1
+// there (same weights and order of operations as pull_one), col at the
+// thread's shared-memory column.
 template <int d, class S>
-__device__ __forceinline__ void pull_dir_staged(const typename S::T* cell, const DomDev& D, const float pc[6],
-                                                const float p2c[6], float* col, float& A, float& B) {
+__device__ __forceinline__ void pull_dir_staged(const typename S::T* cell, int oxm, int oxp, const DomDev& D,
+                                                const float pc[6], const float p2c[6], float* col, float& A,
+                                                float& B) {
   using TB = TmaBox<S>;
   constexpr double cx = dcos(d), cy = dsin(d);
   constexpr int sx = sgnd(cx), sy = sgnd(cy);
@@ -651,16 +593,17 @@ __device__ __forceinline__ void pull_dir_staged(const typename S::T* cell, const
   constexpr float axr = (float)ax, ayr = (float)ay;
   constexpr float w1 = axr * ayr, w2 = (1.0f - axr) * ayr, w3 = axr * (1.0f - ayr),
                   w4 = (1.0f - axr) * (1.0f - ayr);
-  constexpr int o1 = -sx - sy * TB::kW, o2 = -sy * TB::kW, o3 = -sx;
+  const int ox = sx > 0 ? oxm : (sx < 0 ? oxp : 0);
+  constexpr int oy = -sy * TB::kRow;
   float a_ = 0.0f, b_ = 0.0f;
 #pragma unroll
   for (int s = 0; s < 6; ++s) {
-    const typename S::T* pl = cell + s * TB::kPlaneElems;
+    const typename S::T* pl = cell + s * TB::kPlane;
     float v;
     if (ax == 0.0 || ay == 0.0) {
-      v = S::raw(pl[o1]);
+      v = S::raw(pl[ox + oy]);
     } else {
-      const float v1 = S::raw(pl[o1]), v2 = S::raw(pl[o2]), v3 = S::raw(pl[o3]), v4 = S::raw(pl[0]);
+      const float v1 = S::raw(pl[ox + oy]), v2 = S::raw(pl[oy]), v3 = S::raw(pl[ox]), v4 = S::raw(pl[0]);
       v = fmaf(w1, v1, fmaf(w2, v2, fmaf(w3, v3, w4 * v4)));
     }
     v = S::decf(v, D, s);
@@ -676,7 +619,6 @@ template <int EDF, class S>
 __global__ void __launch_bounds__(kThreads, RLBM_MIXED_MIN_BLOCKS) k_step_mixed_tma(StepArgs a) {
   using T = typename S::T;
   using TB = TmaBox<S>;
-  constexpr bool kCol = sizeof(T) == sizeof(float);  // bulk store of the collided tile
   extern __shared__ __align__(128) unsigned char smt[];
   unsigned char* ring = smt;
   float* smf = reinterpret_cast<float*>(smt + kStages * TB::kBytes);
@@ -700,8 +642,11 @@ __global__ void __launch_bounds__(kThreads, RLBM_MIXED_MIN_BLOCKS) k_step_mixed_
       ++issued[d];
     }
   }
-  // the cell's own value in shell 0 of stage 0, and its column
-  const T* cell0 = reinterpret_cast<const T*>(ring) + (threadIdx.y + 1) * TB::kW + threadIdx.x + TB::kLpad;
+  // the cell's own value in shell 0 of stage 0 (row ty + 1, middle block, lane
+  // tx), the offsets of its x neighbours, and its column
+  const T* cell0 = reinterpret_cast<const T*>(ring) + (threadIdx.y + 1) * TB::kRow + TB::kBlock + threadIdx.x;
+  const int oxm = threadIdx.x > 0 ? -1 : -TB::kBlock + (kBlkW - 1);
+  const int oxp = threadIdx.x < kBlkW - 1 ? 1 : TB::kBlock - (kBlkW - 1);
   float* col = smf + tid;
   float pc[6], p2c[6];
 #pragma unroll
@@ -716,10 +661,6 @@ __global__ void __launch_bounds__(kThreads, RLBM_MIXED_MIN_BLOCKS) k_step_mixed_
     const int x = tl.x0 + threadIdx.x, y = tl.y0 + threadIdx.y;
     const int tnext = t + gridDim.x;
     const unsigned use0 = it * (12 / kStages);
-    if (kCol && t != (int)blockIdx.x) {  // the previous tile's bulk store has read the column
-      if (tid == 0) bulk_wait_read();
-      __syncthreads();
-    }
     float A[12], B[12];
     // every lane pulls (lanes outside the domain read the box's padding and
     // fill only their own column, which is never stored)
@@ -727,7 +668,7 @@ __global__ void __launch_bounds__(kThreads, RLBM_MIXED_MIN_BLOCKS) k_step_mixed_
   {                                                                                             \
     constexpr int k_ = (d) % kStages;                                                           \
     const bool ok_ = mbar_wait(&bar[k_], (use0 + (d) / kStages) & 1, wait_ns);                  \
-    pull_dir_staged<d, S>(cell0 + k_ * TB::kStageElems, D, pc, p2c, col, A[d], B[d]);           \
+    pull_dir_staged<d, S>(cell0 + k_ * TB::kStageElems, oxm, oxp, D, pc, p2c, col, A[d], B[d]); \
     if (__syncthreads_or(!ok_)) goto timed_out;                                                 \
     if (tid == 0) {                                                                             \
       inflight &= ~(1u << k_);                                                                  \
@@ -745,25 +686,10 @@ __global__ void __launch_bounds__(kThreads, RLBM_MIXED_MIN_BLOCKS) k_step_mixed_
 #undef RLBM_STAGED_DIR
     if (x < D.nx && y < D.ny) {
       T* __restrict__ fout = static_cast<T*>(a.fout) + D.off;
-      const long long c = (long long)(y + 1) * D.pitch + D.lpad + x;
-      const unsigned st = collide_mixed<EDF, S, kCol>(D, x, y, c, A, B, smf, tid, fout);
+      const unsigned st = collide_mixed<EDF, S>(D, x, y, cell_rel(D, x, y), A, B, smf, tid, fout);
       if (st) atomicOr(a.status, st);
-      if constexpr (kCol) {  // the bulk store covers x < nx & ~3 (16-byte clipping)
-        if (x >= (D.nx & ~3))
-          for (int q = 0; q < 72; ++q) fout[q * D.plane + c] = col[q * kThreads];
-      }
-    }
-    if constexpr (kCol) {
-      fence_async_smem();
-      __syncthreads();
-      if (tid == 0) {
-        const void* smap = static_cast<const unsigned char*>(a.tmaps_out) + (size_t)tl.dom * kTensorMapBytes;
-        tma_store_3d(smap, smf, tl.x0, tl.y0, 0);
-        bulk_commit();
-      }
     }
   }
-  if (kCol && tid == 0) bulk_wait_all();
   return;
 timed_out:
   // a copy did not land in time: report it, let the copies still in flight
@@ -771,19 +697,11 @@ timed_out:
   // above) so that none writes shared memory after exit, return
   if (tid == 0) {
     atomicOr(a.status, ST_TIMEOUT);
-    if (kCol) bulk_wait_all();
 #pragma unroll
     for (int k = 0; k < kStages; ++k)
       if (inflight & (1u << k)) mbar_wait(&bar[k], (issued[k] - 1) & 1);
   }
 }
-
-}  // namespace rlbm
-
-#include "rlbm_lean.cuh"
-#include "rlbm_staged.cuh"
-
-namespace rlbm {
 
 // f = f^eq of the given fields in a mixed storage (time zero), halo included:
 // the collision's FP32 equilibrium deviations (dz_moments, dfeq_shell, with the
@@ -815,8 +733,7 @@ __global__ void __launch_bounds__(kThreads) k_init_mixed(InitArgs a) {
   if (!ok) st |= ST_NONPHYSICAL;
   const float gam = ok ? 1.0f / sqrtf(1.0f - u2) : 1.0f;
   typename S::T* __restrict__ f = static_cast<typename S::T*>(a.f) + D.off;
-  const long long c = (long long)(y + 1) * D.pitch + D.lpad + x;
-  const long long P = D.plane;
+  const long long c = cell_rel(D, x, y);
   float* col = smi + tid;
   if (ok) {
     float zr[21], zi[21];
@@ -844,16 +761,16 @@ __global__ void __launch_bounds__(kThreads) k_init_mixed(InitArgs a) {
       for (int d = 0; d < 12; ++d) {
         const int q = 6 * d + s;
         col[q * kThreads] = fe[d];
-        f[q * P + c] = S::encf(fe[d], D, s);
+        f[q * kBlkW + c] = S::encf(fe[d], D, s);
       }
     }
   } else {
     for (int q = 0; q < 72; ++q) {
       col[q * kThreads] = __int_as_float(0x7fc00000);  // NaN
-      f[q * P + c] = S::encf(col[q * kThreads], D, q % 6);
+      f[q * kBlkW + c] = S::encf(col[q * kThreads], D, q % 6);
     }
   }
-  write_halo_mixed<EDF, S, true>(D, x, y, f, col, ok, n, ux, uy, gam, st);
+  write_halo_mixed<EDF, S>(D, x, y, f, col, ok, n, ux, uy, gam, st);
   if (st) atomicOr(a.status, st);
 }
 
@@ -935,12 +852,6 @@ static cudaError_t prepare_tma_t() {
 template <class S>
 static cudaError_t prepare_s() {
   cudaError_t e;
-  if ((e = prepare_staged_t<S, EDF_MJ>())) return e;
-  if ((e = prepare_staged_t<S, EDF_FD>())) return e;
-  if ((e = prepare_staged_t<S, EDF_BE>())) return e;
-  if ((e = prepare_lean_t<S, EDF_MJ>())) return e;
-  if ((e = prepare_lean_t<S, EDF_FD>())) return e;
-  if ((e = prepare_lean_t<S, EDF_BE>())) return e;
   if ((e = prepare_tma_t<S, EDF_MJ>())) return e;
   if ((e = prepare_tma_t<S, EDF_FD>())) return e;
   if ((e = prepare_tma_t<S, EDF_BE>())) return e;
@@ -978,9 +889,6 @@ static cudaError_t upload_mixed_tables() {
 
 template <class S>
 static cudaError_t step_s(int edf, const StepArgs& a, int grid, cudaStream_t s) {
-  if (a.variant == kVariantLean || a.variant == kVariantLean2)
-    return launch_lean<S>(edf, a.variant == kVariantLean2 ? 2 : 1, a, grid, s);
-  if (a.variant == kVariantStaged) return a.tmaps ? launch_staged<S>(edf, a, grid, s) : cudaErrorInvalidValue;
   if (a.tmaps) {  // TMA-staged variant; without descriptors the pull goes through L1
     const size_t sm = tma_smem_bytes<S>();
     switch (edf) {

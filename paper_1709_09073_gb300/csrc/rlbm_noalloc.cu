@@ -76,9 +76,8 @@ int check_domain(const rlbm_domain* d, int edf) {
 }
 
 // Lay one FP64 domain out inside the scratch array: status word, descriptor,
-// tile list, two halo-padded population copies (each row 16-byte aligned at
-// x = 0, pitch a multiple of 128 bytes). Returns RLBM_E_SCRATCH if it does
-// not fit.
+// tile list, two population copies (blocks of 32 cells, halo ring included,
+// the library's layout). Returns RLBM_E_SCRATCH if it does not fit.
 int plan_scratch(const rlbm_domain* d, ScratchPlan& P) {
   // any side beyond 2^20 cells is far past the limit; this also bounds the arithmetic below
   if (d->nx > (1 << 20) || d->ny > (1 << 20)) return RLBM_E_SCRATCH;
@@ -86,9 +85,8 @@ int plan_scratch(const rlbm_domain* d, ScratchPlan& P) {
   D = DomDev{};
   D.nx = d->nx;
   D.ny = d->ny;
-  D.lpad = 2;                                               // 16 bytes of FP64
-  D.pitch = (int)round_up((size_t)(D.lpad + d->nx + 1), 16);  // 128 bytes of FP64
-  D.plane = (long long)D.pitch * (d->ny + 2);
+  D.nblk = blocks_per_row(d->nx);
+  D.pitch = (long long)D.nblk * kBlk;
   D.off = 0;
   D.bc[0] = d->bc_xlo; D.bc[1] = d->bc_xhi; D.bc[2] = d->bc_ylo; D.bc[3] = d->bc_yhi;
   D.inv_tau = 1.0 / d->tau;
@@ -108,7 +106,7 @@ int plan_scratch(const rlbm_domain* d, ScratchPlan& P) {
   b = round_up(b + sizeof(DomDev), kAlignB);
   P.tiles_off = b;
   b = round_up(b + sizeof(Tile) * (size_t)P.ntiles, kAlignB);
-  const size_t pop_bytes = round_up(72 * (size_t)D.plane * sizeof(double), kAlignB);
+  const size_t pop_bytes = round_up((size_t)(d->ny + 2) * (size_t)D.pitch * sizeof(double), kAlignB);
   P.pop_off[0] = b;
   P.pop_off[1] = b + pop_bytes;
   P.total = b + 2 * pop_bytes;
@@ -184,7 +182,6 @@ extern "C" int rlbm_step_noalloc(const rlbm_domain* domain, int edf, int nsteps,
     a.fout = pop[1 - cur];
     a.status = d_status;
     a.tmaps = nullptr;
-    a.tmaps_out = nullptr;
     a.variant = 0;
     a.wait_ns = 0;
     e = launch_step_f64(edf, a, P.ntiles, s);

@@ -1,9 +1,8 @@
 // Tensor-memory-accelerator (TMA) copies and mbarrier waits for sm_100-class
 // GPUs, as inline PTX: tiled bulk-tensor loads global -> shared memory whose
-// completion is counted in bytes on a shared-memory mbarrier, and tiled
-// bulk-tensor stores shared -> global tracked by bulk async-groups. Every
-// mbarrier wait is bounded in time so that a copy that never lands ends the
-// kernel with an error bit instead of a hang.
+// completion is counted in bytes on a shared-memory mbarrier. Every mbarrier
+// wait is bounded in time so that a copy that never lands ends the kernel with
+// an error bit instead of a hang.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -43,38 +42,16 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
                : "memory");
 }
 
-// 3D tiled copy of one box at element coordinates (x, y, z) of the tensor map
-// (a 64-byte aligned CUtensorMap in global memory) into shared memory.
-__device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, int x, int y, int z, uint64_t* bar) {
+// 4D tiled copy of one box at element coordinates (c0, c1, c2, c3) of the
+// tensor map into shared memory.
+__device__ __forceinline__ void tma_load_4d(void* dst, const void* tmap, int c0, int c1, int c2, int c3,
+                                            uint64_t* bar) {
   asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
       : "memory");
 }
-
-// 3D tiled copy of one box from shared memory to the tensor at (x, y, z);
-// elements outside the tensor are not written (along x, in 16-byte units).
-// Completion is tracked by the issuing thread's bulk async-group.
-__device__ __forceinline__ void tma_store_3d(const void* tmap, const void* src, int x, int y, int z) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
-          reinterpret_cast<uint64_t>(tmap)),
-      "r"(x), "r"(y), "r"(z), "r"(smem_u32(src))
-      : "memory");
-}
-
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-
-// The committed bulk stores have finished reading shared memory.
-__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
-
-// The committed bulk stores have completed.
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
-
-// Order this thread's earlier shared-memory writes before later async-proxy
-// (TMA) reads of them.
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 __device__ __forceinline__ bool mbar_test(uint64_t* bar, unsigned parity) {
   uint32_t ok;

@@ -23,7 +23,7 @@ RLBM_W_LANDAU_MAXITER, RLBM_W_CLAMPED_FUGACITY, RLBM_W_NONPHYSICAL, RLBM_W_ZSOLV
 RLBM_E_ARG, RLBM_E_CUDA, RLBM_E_STATE, RLBM_E_UNSUPPORTED, RLBM_E_NOBUFFER = -1, -2, -3, -4, -5
 RLBM_E_SCRATCH = -6
 RLBM_W_DEVICE_TIMEOUT = 16
-RLBM_KERNEL_L1, RLBM_KERNEL_TMA, RLBM_KERNEL_LEAN, RLBM_KERNEL_LEAN2, RLBM_KERNEL_STAGED = 0, 1, 2, 3, 4
+RLBM_KERNEL_L1, RLBM_KERNEL_TMA = 0, 1
 RLBM_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 EXPORTS = ["rlbm_workspace_bytes", "rlbm_create", "rlbm_init", "rlbm_step", "rlbm_moments",
@@ -267,7 +267,7 @@ class Simulation:
         return _check(load().rlbm_tune(self.h, repeats))
 
     def select_kernel(self, kernel=-1):
-        """Select the mixed step variant (RLBM_KERNEL_L1, _TMA, _LEAN, _LEAN2, _STAGED) or,
+        """Select the mixed step variant (RLBM_KERNEL_L1 or RLBM_KERNEL_TMA) or,
         with no argument, return the one in use."""
         return _check(load().rlbm_select_kernel(self.h, kernel))
 

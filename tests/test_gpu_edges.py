@@ -7,8 +7,8 @@
 * A single cell boxed in by fixed-temperature walls, and one-row and
   one-column domains, agree with the oracle to 1e-12.
 * Zero steps change nothing and launch nothing.
-* A domain narrower than 4 cells gets no TMA descriptors, so its handle
-  refuses the TMA-staged variant."""
+* A domain narrower than 4 cells runs both step variants (the TMA boxes
+  span whole 32-cell blocks)."""
 import numpy as np
 import pytest
 
@@ -72,12 +72,12 @@ def test_zero_steps_change_nothing(R):
     sim.close()
 
 
-def test_narrow_domain_has_no_tma_variant(R):
+def test_narrow_domain_runs_both_variants(R):
     sim = R.Simulation([W.DomainSpec(3, 8, 0.9, 0)], storage=R.RLBM_F32DEV)
     sim.init(0, W.random_domain_state(3, 8, 63))
-    with pytest.raises(R.RlbmError):
-        sim.select_kernel(R.RLBM_KERNEL_TMA)
     assert sim.select_kernel() == R.RLBM_KERNEL_L1
+    sim.step(2)
+    assert sim.select_kernel(R.RLBM_KERNEL_TMA) == R.RLBM_KERNEL_TMA
     sim.step(2)
     assert sim.sync_status() == 0
     sim.close()

@@ -1,8 +1,10 @@
 """The TMA-staged variant of the mixed step (RLBM_KERNEL_TMA) against the L1
 variant: the same arithmetic, so the populations (halo ring included) must be
-bit-identical, for every mixed storage and EDF, on ragged walled domains
-(widths not multiples of 4 exercise the bulk store's tail) and on a batch of
-uneven domains under the persistent grid the tuner may pick."""
+bit-identical, for every mixed storage and EDF, on ragged walled domains, on
+domains one to three cells wide, with the local relaxation time, and on a batch
+of uneven domains under the persistent grid the tuner may pick or a fixed
+one. Also the bounded copy waits: a limit that runs out is reported and the
+handle recovers."""
 import numpy as np
 import pytest
 
@@ -49,6 +51,46 @@ def test_tma_matches_l1_bitwise(R, edf, stname):
     assert np.array_equal(a[0], b[0])
 
 
+@pytest.mark.parametrize("nx", [1, 2, 3, 31, 33, 63])
+def test_tma_matches_l1_on_narrow_and_ragged_widths(R, nx):
+    specs = [W.DomainSpec(nx, 9, 0.9, 0), W.DomainSpec(nx, 6, 1.2, 0, (1, 1, 2, 2), (1.0, 1.0, 0.98, 1.02))]
+    inits = [W.random_domain_state(nx, s.ny, 60 + i) for i, s in enumerate(specs)]
+    a, _ = _populations(R, specs, inits, 4, R.RLBM_KERNEL_L1, 7)
+    b, st = _populations(R, specs, inits, 4, R.RLBM_KERNEL_TMA, 7)
+    assert st == 0
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+def test_tma_matches_l1_with_local_tau(R):
+    spec = W.DomainSpec(45, 14, 0.9, 1, (W.FIXED_T_WALL, W.FIXED_T_WALL, W.PERIODIC, W.PERIODIC),
+                        (0.9, 1.1, 1.0, 1.0), eta_s=0.3)
+    init = W.random_domain_state(45, 14, 77, 1, u_amp=0.05, th_amp=0.15)
+    a, _ = _populations(R, [spec], [init], 4, R.RLBM_KERNEL_L1, 9)
+    b, _ = _populations(R, [spec], [init], 4, R.RLBM_KERNEL_TMA, 9)
+    assert np.array_equal(a[0], b[0])
+
+
+@pytest.mark.parametrize("grid", [1, 3, 7])
+def test_tma_matches_l1_on_fixed_persistent_grids(R, grid):
+    specs = [W.DomainSpec(97, 30, 0.9, 1, (2, 2, 0, 0), (0.96, 1.04, 1, 1)), W.DomainSpec(130, 21, 1.4, 1),
+             W.DomainSpec(40, 9, 0.7, 1, (1, 1, 1, 1))]
+    inits = [W.random_domain_state(s.nx, s.ny, 90 + i, 1, u_amp=0.05) for i, s in enumerate(specs)]
+    outs = []
+    for kernel in (R.RLBM_KERNEL_L1, R.RLBM_KERNEL_TMA):
+        sim = R.Simulation(specs, edf=1, storage=4)
+        for i, s in enumerate(inits):
+            sim.init(i, s)
+        assert sim.select_kernel(kernel) == kernel
+        assert sim.set_grid(grid) == grid
+        sim.step(8)
+        assert sim.sync_status() == 0
+        outs.append([sim.get_populations(i) for i in range(len(specs))])
+        sim.close()
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+
+
 def test_tma_matches_l1_on_a_tuned_batch(R):
     specs = [W.DomainSpec(33, 17, 0.7, 0), W.DomainSpec(64, 8, 1.3, 0, (1, 1, 0, 0)),
              W.DomainSpec(101, 40, 0.9, 0, (2, 2, 0, 0), (0.95, 1.05, 1, 1)),
@@ -68,8 +110,7 @@ def test_kernel_selection_rules(R):
         sim.select_kernel(R.RLBM_KERNEL_TMA)  # FP64 storage has no staged variant
     sim.close()
     narrow = R.Simulation([W.DomainSpec(3, 8, 0.9, 0)], storage=R.RLBM_F32DEV)
-    with pytest.raises(R.RlbmError):
-        narrow.select_kernel(R.RLBM_KERNEL_TMA)  # narrower than 4 cells: no descriptors
+    assert narrow.select_kernel(R.RLBM_KERNEL_TMA) == R.RLBM_KERNEL_TMA  # any width: boxes span whole blocks
     with pytest.raises(R.RlbmError):
         narrow.select_kernel(7)
     narrow.close()

@@ -30,7 +30,7 @@ CASES = [
     # (Secs. 3.4, 3.5), whose descriptor fields the entry point fills itself
     (W.FD, WALLS_Y, 45, 19, {}),
     (W.BE, OPEN_X, 37, 11, {}),
-    (W.MJ, PERIODIC, 160, 160, {}),
+    (W.MJ, PERIODIC, 148, 148, {}),
     (W.FD, VWALLS_Y, 40, 12, {"accel": (2e-4, -1e-4), "eta_s": 0.2, "n_wall": 1.03}),
 ]
 
