@@ -212,13 +212,14 @@ def run_native(args):
     # end to end through the public API with host buffers: the packed fields of
     # every domain copied from pinned host memory and initialised in one call
     # (rlbm_init_all), every step followed by a status read-back, the packed
-    # fields of every domain read back (rlbm_moments_all) into pinned memory;
+    # fields n, theta, u of every domain read back (rlbm_moments_all) into
+    # pinned memory;
     # the device buffers they pass through are allocated before the clock starts
     pinned = [torch.from_numpy(np.concatenate([getattr(s, k).reshape(-1) for s in wl.init])).pin_memory()
               for k in ("a", "theta", "ux", "uy")]
     dev_in = [torch.empty(cells, dtype=torch.float64, device="cuda") for _ in range(4)]
-    dev_out = [torch.empty(cells, dtype=torch.float64, device="cuda") for _ in range(5)]
-    out_host = [torch.empty(cells, dtype=torch.float64).pin_memory() for _ in range(5)]
+    dev_out = [torch.empty(cells, dtype=torch.float64, device="cuda") for _ in range(4)]  # n, theta, ux, uy
+    out_host = [torch.empty(cells, dtype=torch.float64).pin_memory() for _ in range(4)]
     e2e_steps = max(1, args.steps)  # the K steps of the device-timed region
     kind = wl.init[0].kind
     barrier(world)
@@ -237,11 +238,11 @@ def run_native(args):
     te = time.perf_counter() - t0
     te = barrier_max(te, world, torch)
     h2d = 4 * 8 * cells
-    d2h = 5 * 8 * cells + 4 * e2e_steps
+    d2h = 4 * 8 * cells + 4 * e2e_steps
     e2e = {"value": round(total_cells * e2e_steps / te / 1e6, 2), "unit": UNIT,
            "h2d_bytes_per_step": int(h2d / e2e_steps), "d2h_bytes_per_step": int(d2h / e2e_steps),
            "steps": e2e_steps, "what": "packed fields from pinned host -> rlbm_init_all -> "
-                                       "(rlbm_step(1) + status read) x K -> rlbm_moments_all -> pinned host"}
+                                       "(rlbm_step(1) + status read) x K -> rlbm_moments_all (n, theta, u) -> pinned host"}
     sim.close()
     del sim, dev_in, dev_out
 

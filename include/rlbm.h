@@ -237,7 +237,7 @@ int rlbm_set_grid(rlbm_handle h, int grid);
  *                   memory through L1 and stores its 72 values (default);
  *  RLBM_KERNEL_TMA  a ring of TMA boxes (one direction's six shell planes of
  *                   the tile's block of 32 cells and its two neighbours, rows
- *                   y0-1 .. y0+4) staged in shared memory, every wait for a
+ *                   y0-1 .. y0+4 of a 32 x 4 tile) staged in shared memory, every wait for a
  *                   copy bounded (rlbm_set_wait_limit). Needs the driver's
  *                   tensor-map encoder. */
 #define RLBM_KERNEL_L1 0

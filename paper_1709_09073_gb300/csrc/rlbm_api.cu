@@ -111,6 +111,9 @@ void make_layout(const rlbm_config* c, Layout& L) {
     D.accel_x = d.accel_x;
     D.accel_y = d.accel_y;
     D.n_wall = d.n_wall;
+    D.inv_tau_f = (float)D.inv_tau;
+    D.eta_s_f = (float)D.eta_s;
+    for (int k = 0; k < 4; ++k) D.t_wall_f[k] = (float)D.t_wall[k];
     off = align_up(off + (size_t)(d.ny + 2) * (size_t)D.pitch, kAlign / es);
     for (int y0 = 0; y0 < d.ny; y0 += kTileH)
       for (int x0 = 0; x0 < d.nx; x0 += kTileW) L.tiles.push_back(Tile{i, x0, y0, 0});
@@ -209,9 +212,9 @@ cudaError_t capture(rlbm_ctx* h, int from, int nsteps, cudaGraphExec_t* out) {
 
 // TMA descriptors of the staged mixed step, written into `out` as
 // [copy][domain]: a 4D tensor {32 lanes, 72 planes, nblk blocks, ny + 2 rows}
-// of the copy's elements (the halo ring included), boxes {32, 6, 3, 6} (one
+// of the copy's elements (the halo ring included), boxes {32, 6, 3, kTileH + 2} (one
 // direction's six shell planes, the tile's block and its neighbours, rows
-// y0-1 .. y0+4), zero fill outside. Returns false if the driver offers no
+// y0-1 .. y0+kTileH), zero fill outside. Returns false if the driver offers no
 // encoder or refuses a descriptor; the handle then has only the L1 variant.
 bool encode_tmaps(const rlbm_ctx* h, std::vector<unsigned char>& out) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;

@@ -53,13 +53,18 @@ struct DomDev {
   float rres[6];            // FP64 reference equilibrium minus fref, per shell
   float a_s[6];             // 16-bit storage: f = fref + a_s * h, a_s = fref * scale
   float b_s[6];             // 1 / a_s
+  float inv_tau_f, eta_s_f;  // inv_tau and eta_s rounded to FP32 (the mixed step issues no FP64)
+  float t_wall_f[4];         // t_wall rounded to FP32
 };
 
 // Cells of one work-list tile along x and y. Every step kernel covers one tile
-// per block and is launched with blocks of kTileW x kTileH threads (the lean
-// two-cell variant with kTileW / 2 x kTileH); the host builds the tile lists
-// (rlbm_create, rlbm_step_noalloc) from the same constants.
-constexpr int kTileW = 32, kTileH = 4;
+// per block and is launched with blocks of kTileW x kTileH threads; the host
+// builds the tile lists (rlbm_create, rlbm_step_noalloc) from the same
+// constants. kTileW is one x block of the population layout.
+#ifndef RLBM_TILE_H
+#define RLBM_TILE_H 4
+#endif
+constexpr int kTileW = 32, kTileH = RLBM_TILE_H;
 
 struct Tile {
   int dom, x0, y0, pad;
@@ -93,10 +98,10 @@ __host__ __device__ constexpr int blocks_per_row(int nx) { return (nx + kBlkW) /
 constexpr int kTensorMapBytes = 128;  // sizeof(CUtensorMap), 64-byte aligned in memory
 
 // TMA box of the staged mixed step: for one direction, the six shell planes of
-// the tile's x block and its two neighbours over rows y0-1 .. y0+4, i.e. a box
-// {32 lanes, 6 planes, 3 blocks, 6 rows} of the 4D tensor
+// the tile's x block and its two neighbours over rows y0-1 .. y0+kTileH, i.e. a
+// box {32 lanes, 6 planes, 3 blocks, kTileH + 2 rows} of the 4D tensor
 // {32 lanes, 72 planes, nblk blocks, ny + 2 rows}.
-constexpr int kBoxRows = 6, kBoxBlocks = 3, kBoxPlanes = 6;
+constexpr int kBoxRows = kTileH + 2, kBoxBlocks = 3, kBoxPlanes = 6;
 constexpr int kBoxElems = kBlkW * kBoxPlanes * kBoxBlocks * kBoxRows;
 
 }  // namespace rlbm

@@ -12,7 +12,7 @@
 namespace rlbm {
 
 constexpr int kThreads = kTileW * kTileH;  // one cell per thread; blocks of one tile
-static_assert(kThreads == 128, "the shared-memory columns and launch bounds assume 128 cells per tile");
+static_assert(kThreads == 128 || kThreads == 256, "tiles of 32 x 4 or 32 x 8 cells");
 
 __host__ __device__ constexpr int sgnd(double v) { return (v > 0.0) - (v < 0.0); }
 __host__ __device__ constexpr double dcos(int d) {

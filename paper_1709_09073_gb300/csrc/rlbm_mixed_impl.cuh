@@ -364,7 +364,7 @@ __device__ void write_halo_mixed(const DomDev& D, int x, int y, typename S::T* _
         fout[q * kBlkW + h] = S::encf(col[q * kThreads], D, q % 6);
       }
     } else {
-      const float tw = (float)D.t_wall[wall[i]];
+      const float tw = D.t_wall_f[wall[i]];
       float z, g[6];
       st |= solve_z_nt_f<EDF>(n, tw, z, g);
       float zr[21], zi[21];
@@ -382,20 +382,52 @@ __device__ void write_halo_mixed(const DomDev& D, int x, int y, typename S::T* _
 constexpr size_t kSmemF = 72 * kThreads * sizeof(float);  // the shared-memory column of a block
 
 #ifndef RLBM_MIXED_MIN_BLOCKS
-// resident 128-thread blocks per SM the register budget must allow: 4 (128 registers)
-// measured fastest on the 2048^2 FP32-deviation case, ahead of 3 (1.13x) and 5 (1.15x)
-#define RLBM_MIXED_MIN_BLOCKS 4
+// resident blocks per SM the register budget must allow: 512 threads (128
+// registers), measured fastest on the 2048^2 FP32-deviation case
+#define RLBM_MIXED_MIN_BLOCKS (512 / kThreads)
 #endif
+// 1: at the start of a tile one thread asks L2 for the tile's own blocks in rows
+// y0-1 .. y0+kTileH (one contiguous segment per row), so that the pull's later
+// directions find them in L2
+#ifndef RLBM_MIXED_L2_PREFETCH
+#define RLBM_MIXED_L2_PREFETCH 1
+#endif
+
+// Relaxation (Eq. 3) of one cell's 72 pulled deviations in its column, shell
+// by shell, stored to fout; kKeep: the relaxed values also go back into the
+// column (warps holding an edge cell, whose halo writer reads them there).
+template <int EDF, class S, bool kKeep>
+__device__ __forceinline__ void relax_cell(const DomDev& D, const float zr[21], const float zi[21], const float om[12],
+                                           float* smf, int tid, long long c, typename S::T* __restrict__ fout) {
+#pragma unroll 1
+  for (int s = 0; s < 6; ++s) {
+    float fe[12];
+    dfeq_shell<EDF>(s, D.rres[s], zr, zi, fe);
+#pragma unroll
+    for (int d = 0; d < 12; ++d) {
+      const int q = 6 * d + s;
+      const float v = smf[q * kThreads + tid];
+      const float r = fmaf(om[d], fe[d] - v, v);
+      if constexpr (kKeep) smf[q * kThreads + tid] = r;
+      fout[q * kBlkW + c] = S::encf(r, D, s);
+    }
+  }
+}
 
 // Collision of one cell (Eqs. 20-25, 10-11 and 3) from its pulled FP32
 // deviations, held in the thread's shared-memory column smf[q * kThreads + tid],
 // and the shell sums A_d = sum_s p_s dv_{6d+s}, B_d = sum_s p_s^2 dv_{6d+s} of
 // each direction; stores f* to fout, writes the cell's halo images and returns
-// its status bits.
+// its status bits. Called by the active lanes of a warp (the lanes of cells
+// inside the domain).
 template <int EDF, class S>
 __device__ __forceinline__ unsigned collide_mixed(const DomDev& D, int x, int y, long long c, const float A[12],
                                                   const float B[12], float* smf, int tid,
                                                   typename S::T* __restrict__ fout) {
+  // a warp with no cell on the domain's edge has no halo images to write: it
+  // skips keeping the relaxed values in the column (uniform per warp)
+  const bool edge = x == 0 || x == D.nx - 1 || y == 0 || y == D.ny - 1;
+  const bool edge_warp = __any_sync(__activemask(), edge);
   const HarmF ha = harmonics_f(A), hb = harmonics_f(B);
   // moment totals in double-float: reference moments + FP32 deviation sums
   const df N0 = df_add(df_make(D.n0_hl[0], D.n0_hl[1]), ha.h0);
@@ -468,28 +500,17 @@ __device__ __forceinline__ unsigned collide_mixed(const DomDev& D, int x, int y,
     zr[4] -= d21r;
     zi[4] -= d21i;
     // constant tau, or the local tau = 4 (eta/s) / theta + 0.2546 of Sec. 3.5
-    float itau = (float)D.inv_tau;
-    if (D.eta_s > 0.0) itau = 1.0f / (4.0f * (float)D.eta_s / theta + 0.2546f);
+    float itau = D.inv_tau_f;
+    if (D.eta_s_f > 0.0f) itau = 1.0f / (4.0f * D.eta_s_f / theta + 0.2546f);
     float om[12];
 #pragma unroll
     for (int d = 0; d < 12; ++d) om[d] = relax_rate(d, gf, uxf, uyf, itau);
-#pragma unroll 1
-    for (int s = 0; s < 6; ++s) {
-      float fe[12];
-      dfeq_shell<EDF>(s, D.rres[s], zr, zi, fe);
-#pragma unroll
-      for (int d = 0; d < 12; ++d) {
-        const int q = 6 * d + s;
-        const float v = smf[q * kThreads + tid];
-        const float r = fmaf(om[d], fe[d] - v, v);
-        smf[q * kThreads + tid] = r;
-        fout[q * kBlkW + c] = S::encf(r, D, s);
-      }
-    }
+    if (edge_warp) relax_cell<EDF, S, true>(D, zr, zi, om, smf, tid, c, fout);
+    else relax_cell<EDF, S, false>(D, zr, zi, om, smf, tid, c, fout);
   } else {
     for (int q = 0; q < 72; ++q) fout[q * kBlkW + c] = S::encf(smf[q * kThreads + tid], D, q % 6);
   }
-  write_halo_mixed<EDF, S>(D, x, y, fout, smf + tid, ok, nf, uxf, uyf, gf, st);
+  if (edge_warp) write_halo_mixed<EDF, S>(D, x, y, fout, smf + tid, ok, nf, uxf, uyf, gf, st);
   return st;
 }
 
@@ -502,6 +523,17 @@ __device__ __forceinline__ void step_tile_mixed(const StepArgs& a, int t, float*
   if (x >= D.nx || y >= D.ny) return;
   const typename S::T* __restrict__ fin = static_cast<const typename S::T*>(a.fin) + D.off;
   typename S::T* __restrict__ fout = static_cast<typename S::T*>(a.fout) + D.off;
+#if RLBM_MIXED_L2_PREFETCH
+  if (tid == 0) {
+    const int r1 = min(tl.y0 + kTileH, D.ny);
+    for (int r = tl.y0 - 1; r <= r1; ++r) {
+      const typename S::T* p = fin + cell_rel(D, tl.x0, r);  // lane 0, plane 0 of the tile's block
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(__cvta_generic_to_global(p)),
+                   "r"((unsigned)(kBlk * sizeof(typename S::T)))
+                   : "memory");
+    }
+  }
+#endif
   const long long c = cell_rel(D, x, y);
   const Nbr nb = neighbours(D, x);
   // pull (FP32, deviation form) with the FP32 deviation moment sums
@@ -543,7 +575,7 @@ __global__ void __launch_bounds__(kThreads, RLBM_MIXED_MIN_BLOCKS) k_step_mixed(
 // ------------------------------------------- TMA-staged variant of the step
 // Per 32 x 4 tile and direction d, one TMA box brings the six shell planes of d
 // for the tile's block of 32 cells and the blocks either side, rows y0-1 ..
-// y0+4, into shared memory (a box {32 lanes, 6 planes, 3 blocks, 6 rows} of the
+// y0+kTileH, into shared memory (a box {32 lanes, 6 planes, 3 blocks, kTileH + 2 rows} of the
 // 4D tensor {32, 72, nblk, ny + 2}); the bilinear pull reads its four
 // neighbours there at fixed offsets (x - 1 of lane 0 and x + 1 of lane 31 in
 // the neighbouring blocks). A ring of kStages boxes keeps the next directions --
@@ -703,6 +735,107 @@ timed_out:
   }
 }
 
+// Macroscopic fields (n, theta, ux, uy, z) of a mixed storage's populations in
+// the collision's own arithmetic -- the FP32 pull and deviation sums, the
+// double-float totals and Landau frame (Eqs. 20-25), the FP32 fugacity solve --
+// written as FP64 (the double-float values exactly). It runs on the FP32 pipe;
+// the FP64 read-out k_fields, at 1/64 of that rate, serves the diagnostics.
+template <int EDF, class S>
+__global__ void __launch_bounds__(kThreads) k_fields_mixed(FieldsArgs a) {
+  int dom, x, y;
+  cell_of_launch(a.tiles, a.dom, dom, x, y);
+  const DomDev& D = a.doms[dom];
+  if (x >= D.nx || y >= D.ny) return;
+  const typename S::T* __restrict__ f = static_cast<const typename S::T*>(a.f) + D.off;
+  const long long c = cell_rel(D, x, y);
+  float A[12], B[12];
+  {
+    float pc[6], p2c[6];
+#pragma unroll
+    for (int s = 0; s < 6; ++s) {
+      pc[s] = c_pf[EDF][s];
+      p2c[s] = c_p2f[EDF][s];
+    }
+    const Nbr nb = neighbours(D, x);
+    const bool streamed = a.streamed != 0;
+#define RLBM_FIELDS_DIR(d)                                                                       \
+  {                                                                                              \
+    float a_ = 0.0f, b_ = 0.0f;                                                                  \
+    _Pragma("unroll") for (int s = 0; s < 6; ++s) {                                              \
+      const typename S::T* pl = f + c + (6 * d + s) * kBlkW;                                     \
+      const float r = streamed ? pull_one<d, float, S>(pl, nb) : S::raw(pl[0]);                  \
+      const float v = S::decf(r, D, s);                                                          \
+      a_ = fmaf(v, pc[s], a_);                                                                   \
+      b_ = fmaf(v, p2c[s], b_);                                                                  \
+    }                                                                                            \
+    A[d] = a_;                                                                                   \
+    B[d] = b_;                                                                                   \
+  }
+    RLBM_FIELDS_DIR(0) RLBM_FIELDS_DIR(1) RLBM_FIELDS_DIR(2) RLBM_FIELDS_DIR(3)
+    RLBM_FIELDS_DIR(4) RLBM_FIELDS_DIR(5) RLBM_FIELDS_DIR(6) RLBM_FIELDS_DIR(7)
+    RLBM_FIELDS_DIR(8) RLBM_FIELDS_DIR(9) RLBM_FIELDS_DIR(10) RLBM_FIELDS_DIR(11)
+#undef RLBM_FIELDS_DIR
+  }
+  const HarmF ha = harmonics_f(A), hb = harmonics_f(B);
+  const df N0 = df_add(df_make(D.n0_hl[0], D.n0_hl[1]), ha.h0);
+  const df H0 = df_add(df_make(D.t00_hl[0], D.t00_hl[1]), hb.h0);
+  df T[6];
+  T[0] = H0;
+  T[1] = df_make(hb.c1, 0.0f);
+  T[2] = df_make(hb.s1, 0.0f);
+  T[3] = df_scale(df_add(H0, hb.c2), 0.5f);
+  T[4] = df_make(0.5f * hb.s2, 0.0f);
+  T[5] = df_scale(df_add(H0, -hb.c2), 0.5f);
+  df ux, uy, eps, gam;
+  unsigned st = landau_df(T, ux, uy, eps, gam);
+  df n = df_make(0.0f, 0.0f);
+  if (!(st & ST_NONPHYSICAL)) {
+    n = df_mul(gam, df_sub(N0, df_add(df_mul(ux, ha.c1), df_mul(uy, ha.s1))));
+    if (!(n.hi > 0.0f) || !isfinite(n.hi)) st |= ST_NONPHYSICAL;
+  }
+  double on = nan(""), oth = nan(""), oux = nan(""), ouy = nan(""), oz = nan("");
+  if (!(st & ST_NONPHYSICAL)) {
+    const float nf = df_to_float(n), ef = df_to_float(eps);
+    float theta, z, g[6];
+    if (EDF == EDF_MJ) {
+      theta = ef / (2.0f * nf);
+      z = nf / (2.0f * kPIf * theta * theta);
+    } else {
+      const float target = 0.5f * kPIf * ef * ef / (nf * nf * nf);
+      const int zs = solve_z_R_f<EDF>(target, z, g);
+      st |= zs;
+      if (zs & ST_CLAMPED) theta = sqrtf(nf / (2.0f * kPIf * g[1]));
+      else theta = 0.5f * g[1] / g[2] * ef / nf;
+    }
+    on = (double)n.hi + (double)n.lo;
+    oux = (double)ux.hi + (double)ux.lo;
+    ouy = (double)uy.hi + (double)uy.lo;
+    oth = theta;
+    oz = z;
+  }
+  const long long i = (a.tiles ? D.foff : 0) + (long long)y * D.nx + x;
+  if (a.n) a.n[i] = on;
+  if (a.theta) a.theta[i] = oth;
+  if (a.ux) a.ux[i] = oux;
+  if (a.uy) a.uy[i] = ouy;
+  if (a.z) a.z[i] = oz;
+  if (st) atomicOr(a.status, st);
+}
+
+// The mixed storages' read-out: the fields in the collision's arithmetic, or
+// the FP64 kernel when diagnostics are asked for.
+template <class S>
+cudaError_t launch_fields_mixed_t(int edf, const FieldsArgs& a, int nx, int ny, cudaStream_t s) {
+  if (a.diag) return launch_fields_t<S>(edf, a, nx, ny, s);
+  const dim3 grid = launch_grid(a.tiles, a.ntiles, nx, ny);
+  switch (edf) {
+    case EDF_MJ: k_fields_mixed<EDF_MJ, S><<<grid, dim3(kTileW, kTileH), 0, s>>>(a); break;
+    case EDF_FD: k_fields_mixed<EDF_FD, S><<<grid, dim3(kTileW, kTileH), 0, s>>>(a); break;
+    default: k_fields_mixed<EDF_BE, S><<<grid, dim3(kTileW, kTileH), 0, s>>>(a); break;
+  }
+  return cudaGetLastError();
+}
+
 // f = f^eq of the given fields in a mixed storage (time zero), halo included:
 // the collision's FP32 equilibrium deviations (dz_moments, dfeq_shell, with the
 // tables' conserved-moment defects removed) from the FP64 input fields. Its
@@ -849,9 +982,19 @@ static cudaError_t prepare_tma_t() {
                               (int)cudaSharedmemCarveoutMaxShared);
 }
 
+template <class S, int EDF>
+static cudaError_t prepare_mixed_t() {
+  cudaError_t e = cudaFuncSetAttribute(k_init_mixed<EDF, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemF);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_step_mixed<EDF, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemF);
+}
+
 template <class S>
 static cudaError_t prepare_s() {
   cudaError_t e;
+  if ((e = prepare_mixed_t<S, EDF_MJ>())) return e;
+  if ((e = prepare_mixed_t<S, EDF_FD>())) return e;
+  if ((e = prepare_mixed_t<S, EDF_BE>())) return e;
   if ((e = prepare_tma_t<S, EDF_MJ>())) return e;
   if ((e = prepare_tma_t<S, EDF_FD>())) return e;
   if ((e = prepare_tma_t<S, EDF_BE>())) return e;
@@ -924,7 +1067,8 @@ static cudaError_t prepare_unit() {
 
 template <class S>
 constexpr MixedUnit mixed_unit() {
-  return MixedUnit{&prepare_unit<S>, &step_s<S>, &launch_init_mixed_t<S>, &launch_fields_t<S>, &launch_copy_t<S>};
+  return MixedUnit{&prepare_unit<S>, &step_s<S>, &launch_init_mixed_t<S>, &launch_fields_mixed_t<S>,
+                   &launch_copy_t<S>};
 }
 
 extern const MixedUnit kMixedF32, kMixedF32Dev, kMixedBF16, kMixedF16;

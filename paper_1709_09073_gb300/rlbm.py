@@ -182,14 +182,17 @@ class Simulation:
 
     def moments_all(self, streamed=True, out=None):
         """n, theta, ux, uy, z of every domain, packed (see init_all): into the
-        five device tensors `out` if given, else returned as host arrays."""
+        device tensors `out` if given (four or five: z is optional), else
+        returned as host arrays."""
         n = sum(d.nx * d.ny for d in self.specs)
         if out is not None:
+            if len(out) not in (4, 5):
+                raise ValueError("outputs: n, theta, ux, uy and optionally z")
             for f in out:
                 if f.dtype != self.torch.float64 or not f.is_cuda or not f.is_contiguous() or f.numel() != n:
                     raise ValueError("outputs must be contiguous float64 CUDA tensors of %d values" % n)
-            _check(load().rlbm_moments_all(self.h, 1 if streamed else 0,
-                                           *[ctypes.c_void_p(f.data_ptr()) for f in out], 1))
+            ptrs = [ctypes.c_void_p(f.data_ptr()) for f in out] + ([None] if len(out) == 4 else [])
+            _check(load().rlbm_moments_all(self.h, 1 if streamed else 0, *ptrs, 1))
             return out
         res = [np.empty(n) for _ in range(5)]
         _check(load().rlbm_moments_all(self.h, 1 if streamed else 0,

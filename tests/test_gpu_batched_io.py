@@ -92,3 +92,29 @@ def test_batched_calls_check_their_arguments(R):
     with pytest.raises(ValueError):
         sim.init_all(0, *short)
     sim.close()
+
+
+@pytest.mark.parametrize("edf", [0, 1, 2])
+@pytest.mark.parametrize("streamed", [True, False])
+def test_mixed_readout_matches_fp64_readout(R, edf, streamed):
+    """The mixed storages read their fields in the collision's arithmetic (FP32
+    pull and sums, double-float totals and Landau frame): the same populations
+    read by the FP64 kernel (through an FP64 handle holding them) agree to
+    FP32-rounding level."""
+    specs, inits = _batch(edf)
+    sim = R.Simulation(specs, edf=edf, storage=4)
+    sim.init_all(inits[0].kind, *_packed(inits))
+    sim.step(5)
+    ref = R.Simulation(specs, edf=edf, storage=0)
+    for i in range(len(specs)):
+        ref.set_populations(i, sim.get_populations(i))
+    for i in range(len(specs)):
+        a = sim.moments(i, streamed=streamed)
+        b = ref.moments(i, streamed=streamed)
+        assert np.max(np.abs(a[0] / b[0] - 1)) <= 1e-6
+        assert np.max(np.abs(a[1] / b[1] - 1)) <= 1e-6
+        umax = max(np.max(np.abs(b[2])), np.max(np.abs(b[3])))
+        assert max(np.max(np.abs(a[2] - b[2])), np.max(np.abs(a[3] - b[3]))) <= 1e-6 * umax
+        assert np.max(np.abs(a[4] / b[4] - 1)) <= 1e-5
+    sim.close()
+    ref.close()
