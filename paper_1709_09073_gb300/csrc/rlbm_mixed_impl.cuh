@@ -129,6 +129,12 @@ __device__ void g_allf(float z, float g[6]) {
 }
 
 // Fugacity from g_3^2/g_2^3 = target (Eq. 25), FP32 safeguarded Newton in mu = ln z.
+// Start: with w = 1/target, the series g_nu = z -+ z^2/2^nu + z^3/3^nu + ... gives
+// ln(1/target) = mu + s z/2 + c z^2 + O(z^3), s = -1 (FD) or +1 (BE),
+// c = 2/27 - 1/64 - 1/3 + 3/32, so mu = ln w - s w/2 + (1/4 - c) w^2 + O(w^3) for
+// small w; two Newton steps then reach the FP32 floor. On convergence the g of
+// the last evaluation is kept with its own z (its mu is within the last step,
+// < 4e-7, of the root).
 template <int EDF>
 __device__ int solve_z_R_f(float target, float& z, float g[6]) {
   if (EDF == EDF_BE && target < kRZCf) {
@@ -139,20 +145,36 @@ __device__ int solve_z_R_f(float target, float& z, float g[6]) {
   }
   float lo = -40.0f, hi = (EDF == EDF_BE) ? -1.0e-7f : 40.0f;
   const float lt = logf(target);
-  float mu = fminf(fmaxf(-lt, lo + 1e-3f), hi);
+  float mu = -lt;
+  {
+    const float w = 1.0f / target;
+    if (w < 0.5f) {
+      constexpr float kS = EDF == EDF_BE ? 1.0f : -1.0f;
+      constexpr float kC2 = 0.25f - (2.0f / 27.0f - 1.0f / 64.0f - 1.0f / 3.0f + 3.0f / 32.0f);
+      mu = fmaf(fmaf(kC2, w, -0.5f * kS), w, mu);
+    }
+  }
+  mu = fminf(fmaxf(mu, lo + 1e-3f), hi);
   int st = ST_ZSOLVE;
   float dprev = INFINITY;
   for (int it = 0; it < 40; ++it) {
-    g_allf<EDF>(expf(mu), g);
+    const float ze = expf(mu);
+    g_allf<EDF>(ze, g);
     const float F = logf(g[2] * g[2] / (g[1] * g[1] * g[1])) - lt;
-    if (F == 0.0f) { st = 0; break; }
+    if (F == 0.0f) {
+      z = ze;
+      return 0;
+    }
     const float dF = 2.0f * g[1] / g[2] - 3.0f * g[0] / g[1];
     if (F > 0.0f) lo = mu; else hi = mu;
     float mn = mu - F / dF;
     if (!(mn >= lo && mn <= hi)) mn = 0.5f * (lo + hi);
     const float d = fabsf(mn - mu);
+    if (d <= 4e-7f * fmaxf(1.0f, fabsf(mn)) || (d < 1e-4f && d >= dprev)) {
+      z = ze;
+      return 0;
+    }
     mu = mn;
-    if (d <= 4e-7f * fmaxf(1.0f, fabsf(mu)) || (d < 1e-4f && d >= dprev)) { st = 0; break; }
     dprev = d;
   }
   z = expf(mu);
@@ -353,8 +375,9 @@ __device__ __forceinline__ void dz_moments(const DomDev& D, const float g[6], fl
 // global memory instead would put a read-after-write round trip to L2 on every
 // edge warp, which costs more than keeping the column up to date.
 template <int EDF, class S>
-__device__ void write_halo_mixed(const DomDev& D, int x, int y, typename S::T* __restrict__ fout, const float* col,
-                                 bool have_state, float n, float ux, float uy, float gam, unsigned& st) {
+__device__ __noinline__ void write_halo_mixed(const DomDev& D, int x, int y, typename S::T* __restrict__ fout,
+                                              const float* col, bool have_state, float n, float ux, float uy,
+                                              float gam, unsigned& st) {
   int hx[8], hy[8], wall[8];
   const int cnt = halo_targets(D, x, y, hx, hy, wall);
   for (int i = 0; i < cnt; ++i) {
@@ -391,6 +414,15 @@ constexpr size_t kSmemF = 72 * kThreads * sizeof(float);  // the shared-memory c
 // directions find them in L2
 #ifndef RLBM_MIXED_L2_PREFETCH
 #define RLBM_MIXED_L2_PREFETCH 1
+#endif
+// 1: only warps holding an edge cell keep the relaxed values in the column (a
+// second copy of the relaxation loop); 0: every warp keeps them (one loop)
+#ifndef RLBM_MIXED_EDGE_WARPS
+#define RLBM_MIXED_EDGE_WARPS 0
+#endif
+// > 0: also ask L2 for the tile that many places ahead in the work list
+#ifndef RLBM_MIXED_L2_PREFETCH_AHEAD
+#define RLBM_MIXED_L2_PREFETCH_AHEAD 0
 #endif
 
 // Relaxation (Eq. 3) of one cell's 72 pulled deviations in its column, shell
@@ -505,13 +537,30 @@ __device__ __forceinline__ unsigned collide_mixed(const DomDev& D, int x, int y,
     float om[12];
 #pragma unroll
     for (int d = 0; d < 12; ++d) om[d] = relax_rate(d, gf, uxf, uyf, itau);
+#if RLBM_MIXED_EDGE_WARPS
     if (edge_warp) relax_cell<EDF, S, true>(D, zr, zi, om, smf, tid, c, fout);
     else relax_cell<EDF, S, false>(D, zr, zi, om, smf, tid, c, fout);
+#else
+    relax_cell<EDF, S, true>(D, zr, zi, om, smf, tid, c, fout);
+#endif
   } else {
     for (int q = 0; q < 72; ++q) fout[q * kBlkW + c] = S::encf(smf[q * kThreads + tid], D, q % 6);
   }
   if (edge_warp) write_halo_mixed<EDF, S>(D, x, y, fout, smf + tid, ok, nf, uxf, uyf, gf, st);
   return st;
+}
+
+// Ask L2 for a tile's own blocks in rows y0-1 .. y0+kTileH of every plane: one
+// contiguous segment per row, one bulk prefetch each.
+template <class S>
+__device__ __forceinline__ void prefetch_tile_l2(const DomDev& D, const Tile& tl, const typename S::T* fin) {
+  const int r1 = min(tl.y0 + kTileH, D.ny);
+  for (int r = tl.y0 - 1; r <= r1; ++r) {
+    const typename S::T* p = fin + cell_rel(D, tl.x0, r);  // lane 0, plane 0 of the tile's block
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(__cvta_generic_to_global(p)),
+                 "r"((unsigned)(kBlk * sizeof(typename S::T)))
+                 : "memory");
+  }
 }
 
 // One 32 x 4 tile of the step: pull, collide, store (the thread's cell).
@@ -524,15 +573,14 @@ __device__ __forceinline__ void step_tile_mixed(const StepArgs& a, int t, float*
   const typename S::T* __restrict__ fin = static_cast<const typename S::T*>(a.fin) + D.off;
   typename S::T* __restrict__ fout = static_cast<typename S::T*>(a.fout) + D.off;
 #if RLBM_MIXED_L2_PREFETCH
-  if (tid == 0) {
-    const int r1 = min(tl.y0 + kTileH, D.ny);
-    for (int r = tl.y0 - 1; r <= r1; ++r) {
-      const typename S::T* p = fin + cell_rel(D, tl.x0, r);  // lane 0, plane 0 of the tile's block
-      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(__cvta_generic_to_global(p)),
-                   "r"((unsigned)(kBlk * sizeof(typename S::T)))
-                   : "memory");
-    }
+  if (tid == 0) prefetch_tile_l2<S>(D, tl, fin);
+#if RLBM_MIXED_L2_PREFETCH_AHEAD > 0
+  if (tid == kBlkW && t + RLBM_MIXED_L2_PREFETCH_AHEAD < a.ntiles) {  // lane 0 of the second warp
+    const Tile tn = a.tiles[t + RLBM_MIXED_L2_PREFETCH_AHEAD];
+    const DomDev& Dn = a.doms[tn.dom];
+    prefetch_tile_l2<S>(Dn, tn, static_cast<const typename S::T*>(a.fin) + Dn.off);
   }
+#endif
 #endif
   const long long c = cell_rel(D, x, y);
   const Nbr nb = neighbours(D, x);
