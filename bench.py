@@ -380,6 +380,7 @@ def run_profile_case(args):
     """A small case for ncu: init and a few steps of one kernel.
     mixed: 2048 x 2048 Taylor-Green, MJ, FP32 deviations (2.4 GB of populations);
     batch: the first 48 domains of the headline batch (4.5 M cells, 2.6 GB);
+    fourier: the first 16 domains of the FD Fourier batch in BF16 deviations (4.2 M cells, 1.2 GB);
     fp64:  1024 x 1024 Taylor-Green, MJ, FP64 (1.2 GB). Inputs exceed L2."""
     import torch
     from paper_1709_09073_gb300 import build, rlbm
@@ -389,11 +390,15 @@ def run_profile_case(args):
         storage = rlbm.RLBM_F32DEV
         full = W.batched_taylor_green()
         wl = W.Workload(full.name + "_first48", full.domains[:48], full.init[:48], 3)
+    elif args.profile_case == "fourier":
+        storage = rlbm.RLBM_BF16DEV
+        full = W.batched_fourier()
+        wl = W.Workload(full.name + "_first16", full.domains[:16], full.init[:16], 3)
     else:
         L, storage = (2048, rlbm.RLBM_F32DEV) if args.profile_case == "mixed" else (1024, rlbm.RLBM_F64)
         wl = W.taylor_green(L=L, u0=0.02, tau=0.9, steps=3)
     sim, _ = rlbm.from_workload(wl, storage=storage)
-    if args.profile_case in ("mixed", "batch"):
+    if args.profile_case in ("mixed", "batch", "fourier"):
         sim.select_kernel({"l1": rlbm.RLBM_KERNEL_L1, "tma": rlbm.RLBM_KERNEL_TMA}[args.kernel])
     sim.step(3)
     torch.cuda.synchronize()
@@ -573,7 +578,7 @@ def main():
                     help="mixed step variant of --profile-case mixed")
     ap.add_argument("--peaks", action="store_true",
                     help="print the measured FP64/FP32 FMA throughput of the GPU and exit")
-    ap.add_argument("--profile-case", choices=["mixed", "batch", "fp64"], default=None,
+    ap.add_argument("--profile-case", choices=["mixed", "batch", "fourier", "fp64"], default=None,
                     help="run a small single-domain case for ncu instead of the benchmark")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -227,8 +227,10 @@ int rlbm_tune(rlbm_handle h, int repeats);
 
 /* Launch the step kernel with `grid` blocks in later rlbm_step calls: a
  * persistent grid, each block walking the tile list with stride `grid`, or
- * one block per 32 x 4 tile for grid = 0 (the default). rlbm_tune sets it as
- * well. Returns the grid now in use (grid >= 0) or RLBM_E_ARG. */
+ * one block per tile for grid = 0 (the default). The mixed L1 step walks a
+ * list in which each domain's ragged last block of w <= 16 cells is packed,
+ * 32 / w rows per warp; the other kernels walk 32 x 4 tiles. rlbm_tune sets it
+ * as well. Returns the grid now in use (grid >= 0) or RLBM_E_ARG. */
 int rlbm_set_grid(rlbm_handle h, int grid);
 
 /* Variants of the mixed-precision step kernel; both compute the same update

@@ -35,10 +35,11 @@ size_t elem_size(int storage) {
 
 struct Layout {
   size_t esize = 0;
-  size_t status_off = 0, doms_off = 0, tiles_off = 0, tmaps_off = 0, pop_off[2] = {0, 0};
+  size_t status_off = 0, doms_off = 0, tiles_off = 0, ptiles_off = 0, tmaps_off = 0, pop_off[2] = {0, 0};
   size_t pop_elems = 0, pop_bytes = 0, total = 0;
   std::vector<DomDev> dd;
-  std::vector<Tile> tiles;
+  std::vector<Tile> tiles;   // kTileW x kTileH tiles: every kernel but the mixed L1 step
+  std::vector<Tile> ptiles;  // the same with each domain's ragged last x block packed (Tile::w)
 };
 
 bool valid_bc(int b) {
@@ -87,6 +88,7 @@ void make_layout(const rlbm_config* c, Layout& L) {
   long long foff = 0;  // cells before the domain in packed field arrays
   L.dd.resize(c->ndomains);
   L.tiles.clear();
+  L.ptiles.clear();
   for (int i = 0; i < c->ndomains; ++i) {
     const rlbm_domain& d = c->domains[i];
     DomDev& D = L.dd[i];
@@ -115,8 +117,19 @@ void make_layout(const rlbm_config* c, Layout& L) {
     D.eta_s_f = (float)D.eta_s;
     for (int k = 0; k < 4; ++k) D.t_wall_f[k] = (float)D.t_wall[k];
     off = align_up(off + (size_t)(d.ny + 2) * (size_t)D.pitch, kAlign / es);
-    for (int y0 = 0; y0 < d.ny; y0 += kTileH)
-      for (int x0 = 0; x0 < d.nx; x0 += kTileW) L.tiles.push_back(Tile{i, x0, y0, 0});
+    // row bands of tiles, in the same order in both lists; in the packed list a
+    // ragged last block of w <= kPackMaxW cells becomes one tile per
+    // kTileH * (32 / w) rows, placed after the first band it covers
+    const int xl = (d.nx - 1) / kTileW * kTileW, wl = d.nx - xl;
+    const int pw = wl <= kPackMaxW ? wl : 0;
+    const int prow = kTileH * packed_rows_per_warp(pw);
+    for (int y0 = 0; y0 < d.ny; y0 += kTileH) {
+      for (int x0 = 0; x0 < d.nx; x0 += kTileW) {
+        L.tiles.push_back(Tile{i, x0, y0, 0});
+        if (x0 < xl || !pw) L.ptiles.push_back(Tile{i, x0, y0, 0});
+        else if (y0 % prow == 0) L.ptiles.push_back(Tile{i, x0, y0, pw});
+      }
+    }
   }
   L.pop_elems = off;
   L.pop_bytes = align_up(off * es, kAlign);
@@ -127,6 +140,8 @@ void make_layout(const rlbm_config* c, Layout& L) {
   b = align_up(b + sizeof(DomDev) * L.dd.size(), kAlign);
   L.tiles_off = b;
   b = align_up(b + sizeof(Tile) * L.tiles.size(), kAlign);
+  L.ptiles_off = b;
+  b = align_up(b + sizeof(Tile) * L.ptiles.size(), kAlign);
   // TMA descriptors of the staged mixed step: [copy][domain]
   L.tmaps_off = b;
   if (c->storage != RLBM_F64) b = align_up(b + 2 * (size_t)kTensorMapBytes * L.dd.size(), kAlign);
@@ -149,6 +164,7 @@ struct rlbm_ctx {
   unsigned* d_status = nullptr;
   DomDev* d_doms = nullptr;
   Tile* d_tiles = nullptr;
+  Tile* d_ptiles = nullptr;          // the packed tile list (Layout::ptiles)
   unsigned char* d_tmaps = nullptr;  // null unless the TMA-staged variant is available
   void* pop[2] = {nullptr, nullptr};
   int cur = 0;
@@ -162,17 +178,24 @@ struct rlbm_ctx {
   int grid = 0;                  // blocks of the step kernel (0 = one per tile)
   int kernel = RLBM_KERNEL_L1;   // mixed step variant (rlbm_select_kernel)
   unsigned long long wait_ns = 0;  // TMA copy-wait limit (0: the default, rlbm_set_wait_limit)
+  bool images_stale = false;     // the current copy lacks its periodic halo images (fill_images)
 };
 
 namespace {
 
 int cuda_fail(cudaError_t e) { return e == cudaSuccess ? RLBM_OK : RLBM_E_CUDA; }
 
+// The tile list a step launch walks: the packed one for the mixed step's L1
+// pull, the plain one for the TMA-staged variant (whose boxes assume 32 x
+// kTileH tiles) and the FP64 step.
+bool packed_tiles(const rlbm_ctx* h) { return h->storage != RLBM_F64 && h->kernel == RLBM_KERNEL_L1; }
+
 cudaError_t launch_step(rlbm_ctx* h, int from) {
   StepArgs a;
   a.doms = h->d_doms;
-  a.tiles = h->d_tiles;
-  a.ntiles = (int)h->L.tiles.size();
+  const bool pk = packed_tiles(h);
+  a.tiles = pk ? h->d_ptiles : h->d_tiles;
+  a.ntiles = (int)(pk ? h->L.ptiles.size() : h->L.tiles.size());
   a.fin = h->pop[from];
   a.fout = h->pop[1 - from];
   a.status = h->d_status;
@@ -291,10 +314,60 @@ __global__ void k_rows(RowArgs a) {
     // received rows: y = -1 gets planes 6.., y = ny gets planes 42..
     const int q0 = (side == 0) == (a.unpack != 0) ? kPlanesUp : kPlanesDown;
     const int y = a.unpack ? (side ? a.D.ny : -1) : (side ? a.D.ny - 1 : 0);
-    const long long idx = cell_pos(a.D, (int)xx - 1, y) + (q0 + k) * kBlkW;
+    int x = (int)xx - 1;
+    // a sent row's periodic x ghosts are its wrapped end cells (the L1 step
+    // leaves the images unwritten)
+    if (!a.unpack && a.D.bc[0] == BC_PERIODIC) x = x < 0 ? a.D.nx - 1 : (x == a.D.nx ? 0 : x);
+    const long long idx = cell_pos(a.D, x, y) + (q0 + k) * kBlkW;
     if (a.unpack) pop[idx] = buf[r];
     else buf[r] = pop[idx];
   }
+}
+
+// Periodic halo images of every domain of a population copy, copied from the
+// interior cells they map to (raw elements, all 72 planes): pass 0 the x
+// images of rows -1..ny, then pass 1 the y images of columns -1..nx (so the
+// corners take the images of the x ghosts). The result is the halo the
+// producing step would have written with its images on.
+template <class T>
+__global__ void k_images(const DomDev* doms, int ndom, void* pop_, int pass) {
+  T* pop = static_cast<T*>(pop_);
+  for (int dm = blockIdx.y; dm < ndom; dm += gridDim.y) {
+    const DomDev& D = doms[dm];
+    if (D.bc[pass == 0 ? 0 : 2] != BC_PERIODIC) continue;
+    const long long len = pass == 0 ? D.ny + 2 : D.nx + 2, per = 72 * len;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < 2 * per;
+         e += (long long)gridDim.x * blockDim.x) {
+      const int side = e >= per;
+      const long long r = e - side * per;
+      const int q = (int)(r / len), k = (int)(r % len) - 1;
+      long long dst, src;
+      if (pass == 0) {
+        dst = cell_pos(D, side ? D.nx : -1, k);
+        src = cell_pos(D, side ? 0 : D.nx - 1, k);
+      } else {
+        dst = cell_pos(D, k, side ? D.ny : -1);
+        src = cell_pos(D, k, side ? 0 : D.ny - 1);
+      }
+      pop[dst + q * kBlkW] = pop[src + q * kBlkW];
+    }
+  }
+}
+
+cudaError_t fill_images(rlbm_ctx* h) {
+  if (!h->images_stale) return cudaSuccess;
+  const dim3 grid(64, (unsigned)std::min(h->ndom, 65535));
+  for (int pass = 0; pass < 2; ++pass) {
+    switch (h->L.esize) {
+      case 8: k_images<unsigned long long><<<grid, 256, 0, h->stream>>>(h->d_doms, h->ndom, h->pop[h->cur], pass); break;
+      case 4: k_images<unsigned><<<grid, 256, 0, h->stream>>>(h->d_doms, h->ndom, h->pop[h->cur], pass); break;
+      default: k_images<unsigned short><<<grid, 256, 0, h->stream>>>(h->d_doms, h->ndom, h->pop[h->cur], pass); break;
+    }
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  h->images_stale = false;
+  return cudaSuccess;
 }
 
 int slab_rows(rlbm_handle h, int domain, void* lo, void* hi, int unpack) {
@@ -354,6 +427,7 @@ int rlbm_create(const rlbm_config* c, rlbm_handle* out) {
   h->d_status = reinterpret_cast<unsigned*>(h->base + h->L.status_off);
   h->d_doms = reinterpret_cast<DomDev*>(h->base + h->L.doms_off);
   h->d_tiles = reinterpret_cast<Tile*>(h->base + h->L.tiles_off);
+  h->d_ptiles = reinterpret_cast<Tile*>(h->base + h->L.ptiles_off);
   if (h->storage != RLBM_F64) h->d_tmaps = reinterpret_cast<unsigned char*>(h->base + h->L.tmaps_off);
   h->pop[0] = h->base + h->L.pop_off[0];
   h->pop[1] = h->base + h->L.pop_off[1];
@@ -373,6 +447,9 @@ int rlbm_create(const rlbm_config* c, rlbm_handle* out) {
                         cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->d_tiles, h->L.tiles.data(), sizeof(Tile) * h->L.tiles.size(),
+                        cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->d_ptiles, h->L.ptiles.data(), sizeof(Tile) * h->L.ptiles.size(),
                         cudaMemcpyHostToDevice, h->stream);
   std::vector<unsigned char> maps;
   if (e == cudaSuccess && h->d_tmaps && !encode_tmaps(h, maps)) h->d_tmaps = nullptr;
@@ -445,7 +522,9 @@ int rlbm_step(rlbm_handle h, int nsteps) {
   for (char v : h->initialized)
     if (!v) return RLBM_E_STATE;
   int launches = 0;
-  cudaError_t e = cudaSuccess;
+  // the TMA-staged step reads the periodic halo images as stored
+  cudaError_t e = h->storage != RLBM_F64 && h->kernel == RLBM_KERNEL_TMA && nsteps > 0 ? fill_images(h)
+                                                                                        : cudaSuccess;
   int left = nsteps;
   while (left >= 2 * kChunkPairs && e == cudaSuccess) {
     if (!h->chunk_graph[h->cur]) e = capture(h, h->cur, 2 * kChunkPairs, &h->chunk_graph[h->cur]);
@@ -464,6 +543,7 @@ int rlbm_step(rlbm_handle h, int nsteps) {
     h->cur = 1 - h->cur;
     launches += 1;
   }
+  if (nsteps > 0 && packed_tiles(h)) h->images_stale = true;  // the L1 step wraps instead
   h->last_updates = (long long)nsteps * h->cells;
   h->last_launches = launches;
   return cuda_fail(e);
@@ -549,6 +629,7 @@ int rlbm_init_all(rlbm_handle h, int kind, const double* a, const double* theta,
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return RLBM_E_CUDA;
   for (char& v : h->initialized) v = 1;
+  h->images_stale = false;  // the initialisers write every halo cell
   return (int)st;
 }
 
@@ -655,6 +736,7 @@ static int copy_pops(rlbm_handle h, int domain, double* f, int on_device, int to
 
 int rlbm_get_populations(rlbm_handle h, int domain, double* f, int on_device) {
   if (h && domain >= 0 && domain < h->ndom && !h->initialized[domain]) return RLBM_E_STATE;
+  if (h && fill_images(h) != cudaSuccess) return RLBM_E_CUDA;  // a checkpoint holds the whole halo
   return copy_pops(h, domain, f, on_device, 1);
 }
 
@@ -683,8 +765,9 @@ int rlbm_tune(rlbm_handle h, int repeats) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return RLBM_E_CUDA;
-  const int ntiles = (int)h->L.tiles.size();
-  std::vector<int> cand = {ntiles};
+  // grid 0: one block per tile of whichever list the variant walks
+  const int ntiles = (int)h->L.ptiles.size();  // the shorter list
+  std::vector<int> cand = {0};
   for (int k : {1, 2, 3, 4, 6, 8})
     if (k * sms < ntiles) cand.push_back(k * sms);
   // keep the warnings accumulated so far; timing launches must not add any
@@ -698,8 +781,13 @@ int rlbm_tune(rlbm_handle h, int repeats) {
   // kernel variants: the mixed storages with TMA descriptors have two
   std::vector<int> kernels = {RLBM_KERNEL_L1};
   if (h->d_tmaps) kernels.push_back(RLBM_KERNEL_TMA);
+  if (h->d_tmaps && fill_images(h) != cudaSuccess) {  // the TMA candidates time on the stored halo
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    return RLBM_E_CUDA;
+  }
   float best = 1e30f;
-  int best_grid = ntiles, best_kernel = h->kernel;
+  int best_grid = 0, best_kernel = h->kernel;
   for (int kv : kernels)
     for (int g : cand) {
       h->kernel = kv;
@@ -722,6 +810,7 @@ int rlbm_tune(rlbm_handle h, int repeats) {
   cudaEventDestroy(t1);
   h->grid = best_grid;
   h->kernel = best_kernel;
+  if (best_grid == 0) best_grid = (int)(packed_tiles(h) ? h->L.ptiles.size() : h->L.tiles.size());
   drop_graphs(h);
   *h->h_status = saved;
   if (e == cudaSuccess)

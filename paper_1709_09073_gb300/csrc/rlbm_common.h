@@ -66,9 +66,31 @@ struct DomDev {
 #endif
 constexpr int kTileW = 32, kTileH = RLBM_TILE_H;
 
+// A tile of domain `dom` from cell (x0, y0). w = 0: kTileW x kTileH cells, warp
+// k on row y0 + k, lane l on x0 + l. w in 1..kPackMaxW: the ragged last x
+// block of a domain, only w cells wide, packed: each warp covers 32 / w rows of
+// w cells (lane l on x0 + l % w, row y0 + k * (32 / w) + l / w; lanes from
+// (32 / w) * w on idle), so the tile spans kTileH * (32 / w) rows.
 struct Tile {
-  int dom, x0, y0, pad;
+  int dom, x0, y0, w;
 };
+constexpr int kPackMaxW = 16;  // widest ragged block worth packing (two rows per warp)
+
+__host__ __device__ constexpr int packed_rows_per_warp(int w) { return w > 0 ? kTileW / w : 1; }
+
+// Cell of thread (lane, warp) of a tile; false for idle lanes of a packed tile
+// (cells outside the domain are the caller's test).
+__host__ __device__ inline bool tile_cell(const Tile& tl, int lane, int warp, int& x, int& y) {
+  if (tl.w == 0) {
+    x = tl.x0 + lane;
+    y = tl.y0 + warp;
+    return true;
+  }
+  const int r = kTileW / tl.w;
+  x = tl.x0 + lane % tl.w;
+  y = tl.y0 + warp * r + lane / tl.w;
+  return lane < r * tl.w;
+}
 
 struct StepArgs {
   const DomDev* doms;

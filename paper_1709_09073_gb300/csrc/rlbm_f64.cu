@@ -22,7 +22,7 @@ __global__ void __launch_bounds__(kThreads) k_step_f64(StepArgs a) {
     double* __restrict__ fout = static_cast<double*>(a.fout) + D.off;
     const long long c = cell_rel(D, x, y);
     double N[3], T[6];
-    pull_moments64<EDF, StoreF64>(fin, D, x, c, sm, tid, N, T);
+    pull_moments64<EDF, StoreF64>(fin, D, x, y, c, sm, tid, N, T);
     CellState S;
     unsigned st = cell_state<EDF>(N, T, S);
     const bool ok = !(st & ST_NONPHYSICAL);

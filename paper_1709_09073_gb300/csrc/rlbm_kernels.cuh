@@ -80,17 +80,33 @@ struct StoreF32Dev {
 };
 
 // Element offsets, from a cell's own element, of its neighbours x - 1 and
-// x + 1 in the same row (in the next block across a block boundary) and the
-// row stride (y + 1).
+// x + 1 in the same row (in the next block across a block boundary) and of
+// the rows y - 1 and y + 1. Across a periodic side they point at the wrapped
+// interior cell (x = nx - 1 for x - 1 of x = 0, row ny - 1 for y - 1 of row 0,
+// and so on) rather than at the halo image, which holds the same value when
+// it is written: the offsets compose, so a diagonal neighbour wraps in x, in
+// y or in both. Every pull therefore reads no periodic halo image.
 struct Nbr {
-  long long xm, xp, W;
+  int xm, xp;
+  long long ym, yp;
 };
-__device__ __forceinline__ Nbr neighbours(const DomDev& D, int x) {
+__device__ __forceinline__ Nbr neighbours(const DomDev& D, int x, int y) {
   const int lane = (x + kBlkW) % kBlkW;
   Nbr n;
   n.xm = lane ? -1 : -kBlk + (kBlkW - 1);
   n.xp = lane != kBlkW - 1 ? 1 : kBlk - (kBlkW - 1);
-  n.W = D.pitch;
+  if (D.bc[0] == BC_PERIODIC) {
+    const int span = (int)(cell_rel(D, D.nx - 1, 0) - cell_rel(D, 0, 0));
+    if (x == 0) n.xm = span;
+    if (x == D.nx - 1) n.xp = -span;
+  }
+  n.ym = -D.pitch;
+  n.yp = D.pitch;
+  if (D.bc[2] == BC_PERIODIC) {
+    const long long span = (long long)(D.ny - 1) * D.pitch;
+    if (y == 0) n.ym = span;
+    if (y == D.ny - 1) n.yp = -span;
+  }
   return n;
 }
 
@@ -105,7 +121,7 @@ __device__ __forceinline__ R pull_one(const typename S::T* __restrict__ pl, cons
   constexpr int sx = sgnd(cx), sy = sgnd(cy);
   constexpr double ax = dabs(cx), ay = dabs(cy);
   const long long ox = sx > 0 ? nb.xm : (sx < 0 ? nb.xp : 0);  // to x - sx
-  const long long oy = -(long long)sy * nb.W;                   // to y - sy
+  const long long oy = sy > 0 ? nb.ym : (sy < 0 ? nb.yp : 0);   // to y - sy
   if (ax == 0.0 || ay == 0.0) return (R)S::raw(pl[ox + oy]);
   // weights from the rounded |v_x|, |v_y| (one of them is 1/2): every product and
   // 1 - |v| is exact in R, so the four weights sum to exactly 1 and streaming
@@ -121,9 +137,9 @@ __device__ __forceinline__ R pull_one(const typename S::T* __restrict__ pl, cons
 // return N^mu, T^{mu nu} (Eqs. 20, 22).
 template <int EDF, class S>
 __device__ __forceinline__ void pull_moments64(const typename S::T* __restrict__ fin, const DomDev& D,
-                                               int x, long long c, double* sm, int tid, double N[3],
+                                               int x, int y, long long c, double* sm, int tid, double N[3],
                                                double T[6]) {
-  const Nbr nb = neighbours(D, x);
+  const Nbr nb = neighbours(D, x, y);
   double A[12], B[12];
 #define RLBM_PULL_DIR(d)                                                          \
   {                                                                               \
@@ -169,21 +185,25 @@ __device__ __forceinline__ void feq_emit(const double g[6], double theta, double
 // the wall side (-1: copy of the cell, 0..3: fixed-T wall ghost of that side).
 // Periodic: wrapped image; zero-gradient: copy; fixed-T wall: f^eq(n_b, u_b,
 // theta_wall) from the cell's pre-collision state; an x wall wins at corners.
-__device__ __forceinline__ int halo_targets(const DomDev& D, int x, int y, int hx[8], int hy[8], int wall[8]) {
+// images = false leaves out the periodic images (every pull wraps across a
+// periodic side instead, see neighbours); only the TMA-staged step, whose
+// boxes read the halo as stored, needs them.
+__device__ __forceinline__ int halo_targets(const DomDev& D, int x, int y, int hx[8], int hy[8], int wall[8],
+                                            bool images = true) {
   const int nx = D.nx, ny = D.ny;
   int xs[3], ys[3], nX = 1, nY = 1;
   xs[0] = x;
   ys[0] = y;
   if (D.bc[0] == BC_PERIODIC) {
-    if (x == nx - 1) xs[nX++] = -1;
-    if (x == 0) xs[nX++] = nx;
+    if (images && x == nx - 1) xs[nX++] = -1;
+    if (images && x == 0) xs[nX++] = nx;
   } else {
     if (x == 0) xs[nX++] = -1;
     if (x == nx - 1) xs[nX++] = nx;
   }
   if (D.bc[2] == BC_PERIODIC) {
-    if (y == ny - 1) ys[nY++] = -1;
-    if (y == 0) ys[nY++] = ny;
+    if (images && y == ny - 1) ys[nY++] = -1;
+    if (images && y == 0) ys[nY++] = ny;
   } else {
     if (y == 0) ys[nY++] = -1;
     if (y == ny - 1) ys[nY++] = ny;
@@ -367,7 +387,7 @@ __global__ void __launch_bounds__(kThreads) k_fields(FieldsArgs a) {
   const long long c = cell_rel(D, x, y);
   double N[3], T[6];
   if (a.streamed) {
-    pull_moments64<EDF, S>(f, D, x, c, sm, tid, N, T);
+    pull_moments64<EDF, S>(f, D, x, y, c, sm, tid, N, T);
   } else {
     double A[12], B[12];
     for (int d = 0; d < 12; ++d) {

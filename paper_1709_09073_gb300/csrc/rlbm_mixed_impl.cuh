@@ -56,11 +56,20 @@ constexpr float kRZCf = (float)RLBM_R_ZC;
 constexpr float kZCf = 0.9999999f;
 
 // --------------------------------------------------- FP32 EDF integrals g_nu
+// 1: the series loop fully unrolled, its coefficients immediate constant
+// operands; 4: unrolled by four, coefficients loaded per term
+#ifndef RLBM_SERIES_UNROLL
+#define RLBM_SERIES_UNROLL 4
+#endif
 __device__ __forceinline__ void li_series6f(float x, float g[6]) {
   float xk = 1.0f;
 #pragma unroll
   for (int i = 0; i < 6; ++i) g[i] = 0.0f;
+#if RLBM_SERIES_UNROLL == 1
+#pragma unroll
+#else
 #pragma unroll 4
+#endif
   for (int k = 1; k <= kSerF; ++k) {
     xk *= x;
 #pragma unroll
@@ -377,9 +386,9 @@ __device__ __forceinline__ void dz_moments(const DomDev& D, const float g[6], fl
 template <int EDF, class S>
 __device__ __noinline__ void write_halo_mixed(const DomDev& D, int x, int y, typename S::T* __restrict__ fout,
                                               const float* col, bool have_state, float n, float ux, float uy,
-                                              float gam, unsigned& st) {
+                                              float gam, unsigned& st, bool images) {
   int hx[8], hy[8], wall[8];
-  const int cnt = halo_targets(D, x, y, hx, hy, wall);
+  const int cnt = halo_targets(D, x, y, hx, hy, wall, images);
   for (int i = 0; i < cnt; ++i) {
     const long long h = cell_rel(D, hx[i], hy[i]);
     if (wall[i] < 0 || !have_state) {
@@ -420,10 +429,6 @@ constexpr size_t kSmemF = 72 * kThreads * sizeof(float);  // the shared-memory c
 #ifndef RLBM_MIXED_EDGE_WARPS
 #define RLBM_MIXED_EDGE_WARPS 0
 #endif
-// > 0: also ask L2 for the tile that many places ahead in the work list
-#ifndef RLBM_MIXED_L2_PREFETCH_AHEAD
-#define RLBM_MIXED_L2_PREFETCH_AHEAD 0
-#endif
 
 // Relaxation (Eq. 3) of one cell's 72 pulled deviations in its column, shell
 // by shell, stored to fout; kKeep: the relaxed values also go back into the
@@ -451,14 +456,17 @@ __device__ __forceinline__ void relax_cell(const DomDev& D, const float zr[21], 
 // and the shell sums A_d = sum_s p_s dv_{6d+s}, B_d = sum_s p_s^2 dv_{6d+s} of
 // each direction; stores f* to fout, writes the cell's halo images and returns
 // its status bits. Called by the active lanes of a warp (the lanes of cells
-// inside the domain).
-template <int EDF, class S>
+// inside the domain). kImages: also write the periodic halo images (the
+// TMA-staged step reads them; the L1 pull wraps instead).
+template <int EDF, class S, bool kImages>
 __device__ __forceinline__ unsigned collide_mixed(const DomDev& D, int x, int y, long long c, const float A[12],
                                                   const float B[12], float* smf, int tid,
                                                   typename S::T* __restrict__ fout) {
-  // a warp with no cell on the domain's edge has no halo images to write: it
-  // skips keeping the relaxed values in the column (uniform per warp)
-  const bool edge = x == 0 || x == D.nx - 1 || y == 0 || y == D.ny - 1;
+  // a warp with no cell on an edge that has halo cells to write skips the halo
+  // writer (uniform per warp)
+  const bool edge = kImages ? (x == 0 || x == D.nx - 1 || y == 0 || y == D.ny - 1)
+                            : (D.bc[0] != BC_PERIODIC && (x == 0 || x == D.nx - 1)) ||
+                                  (D.bc[2] != BC_PERIODIC && (y == 0 || y == D.ny - 1));
   const bool edge_warp = __any_sync(__activemask(), edge);
   const HarmF ha = harmonics_f(A), hb = harmonics_f(B);
   // moment totals in double-float: reference moments + FP32 deviation sums
@@ -546,7 +554,7 @@ __device__ __forceinline__ unsigned collide_mixed(const DomDev& D, int x, int y,
   } else {
     for (int q = 0; q < 72; ++q) fout[q * kBlkW + c] = S::encf(smf[q * kThreads + tid], D, q % 6);
   }
-  if (edge_warp) write_halo_mixed<EDF, S>(D, x, y, fout, smf + tid, ok, nf, uxf, uyf, gf, st);
+  if (edge_warp) write_halo_mixed<EDF, S>(D, x, y, fout, smf + tid, ok, nf, uxf, uyf, gf, st, kImages);
   return st;
 }
 
@@ -563,27 +571,22 @@ __device__ __forceinline__ void prefetch_tile_l2(const DomDev& D, const Tile& tl
   }
 }
 
-// One 32 x 4 tile of the step: pull, collide, store (the thread's cell).
+// One tile of the step (32 x 4 cells, or a packed ragged block): pull,
+// collide, store (the thread's cell).
 template <int EDF, class S>
 __device__ __forceinline__ void step_tile_mixed(const StepArgs& a, int t, float* smf, int tid) {
   const Tile tl = a.tiles[t];
   const DomDev& D = a.doms[tl.dom];
-  const int x = tl.x0 + threadIdx.x, y = tl.y0 + threadIdx.y;
-  if (x >= D.nx || y >= D.ny) return;
+  int x, y;
+  if (!tile_cell(tl, threadIdx.x, threadIdx.y, x, y) || x >= D.nx || y >= D.ny) return;
   const typename S::T* __restrict__ fin = static_cast<const typename S::T*>(a.fin) + D.off;
   typename S::T* __restrict__ fout = static_cast<typename S::T*>(a.fout) + D.off;
 #if RLBM_MIXED_L2_PREFETCH
-  if (tid == 0) prefetch_tile_l2<S>(D, tl, fin);
-#if RLBM_MIXED_L2_PREFETCH_AHEAD > 0
-  if (tid == kBlkW && t + RLBM_MIXED_L2_PREFETCH_AHEAD < a.ntiles) {  // lane 0 of the second warp
-    const Tile tn = a.tiles[t + RLBM_MIXED_L2_PREFETCH_AHEAD];
-    const DomDev& Dn = a.doms[tn.dom];
-    prefetch_tile_l2<S>(Dn, tn, static_cast<const typename S::T*>(a.fin) + Dn.off);
-  }
-#endif
+  // (a packed tile uses at most half of each block it would fetch: not worth it)
+  if (tid == 0 && tl.w == 0) prefetch_tile_l2<S>(D, tl, fin);
 #endif
   const long long c = cell_rel(D, x, y);
-  const Nbr nb = neighbours(D, x);
+  const Nbr nb = neighbours(D, x, y);
   // pull (FP32, deviation form) with the FP32 deviation moment sums
   float A[12], B[12], pc[6], p2c[6];
 #pragma unroll
@@ -607,7 +610,7 @@ __device__ __forceinline__ void step_tile_mixed(const StepArgs& a, int t, float*
   RLBM_PULL_DIR(4) RLBM_PULL_DIR(5) RLBM_PULL_DIR(6) RLBM_PULL_DIR(7)
   RLBM_PULL_DIR(8) RLBM_PULL_DIR(9) RLBM_PULL_DIR(10) RLBM_PULL_DIR(11)
 #undef RLBM_PULL_DIR
-  const unsigned st = collide_mixed<EDF, S>(D, x, y, c, A, B, smf, tid, fout);
+  const unsigned st = collide_mixed<EDF, S, false>(D, x, y, c, A, B, smf, tid, fout);
   if (st) atomicOr(a.status, st);
 }
 
@@ -766,7 +769,7 @@ __global__ void __launch_bounds__(kThreads, RLBM_MIXED_MIN_BLOCKS) k_step_mixed_
 #undef RLBM_STAGED_DIR
     if (x < D.nx && y < D.ny) {
       T* __restrict__ fout = static_cast<T*>(a.fout) + D.off;
-      const unsigned st = collide_mixed<EDF, S>(D, x, y, cell_rel(D, x, y), A, B, smf, tid, fout);
+      const unsigned st = collide_mixed<EDF, S, true>(D, x, y, cell_rel(D, x, y), A, B, smf, tid, fout);
       if (st) atomicOr(a.status, st);
     }
   }
@@ -804,7 +807,7 @@ __global__ void __launch_bounds__(kThreads) k_fields_mixed(FieldsArgs a) {
       pc[s] = c_pf[EDF][s];
       p2c[s] = c_p2f[EDF][s];
     }
-    const Nbr nb = neighbours(D, x);
+    const Nbr nb = neighbours(D, x, y);
     const bool streamed = a.streamed != 0;
 #define RLBM_FIELDS_DIR(d)                                                                       \
   {                                                                                              \
@@ -951,7 +954,7 @@ __global__ void __launch_bounds__(kThreads) k_init_mixed(InitArgs a) {
       f[q * kBlkW + c] = S::encf(col[q * kThreads], D, q % 6);
     }
   }
-  write_halo_mixed<EDF, S>(D, x, y, f, col, ok, n, ux, uy, gam, st);
+  write_halo_mixed<EDF, S>(D, x, y, f, col, ok, n, ux, uy, gam, st, true);
   if (st) atomicOr(a.status, st);
 }
 
