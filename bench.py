@@ -411,9 +411,9 @@ def run_profile_case(args):
 def run_other_configs(args, hbm_peak):
     """The other throughput configurations of the method on this GPU, each with
     its own autotuned launch: the 8192^2 Bose-Einstein hot spot in FP32
-    deviations and in FP64, and the 64-domain Fermi-Dirac Fourier-flow batch in
-    the 16-bit deviation storages (and in FP32 deviations, for comparison). Device
-    time with CUDA events over K steps
+    deviations and in FP64, the 64-domain Fermi-Dirac Fourier-flow batch in the
+    16-bit deviation storages (and in FP32 deviations, for comparison), and the
+    headline batch in BF16 deviations. Device time with CUDA events over K steps
     after W warm-up steps; inputs exceed L2."""
     import torch
     from paper_1709_09073_gb300 import rlbm
@@ -422,7 +422,8 @@ def run_other_configs(args, hbm_peak):
              ("hot_spot_8192x8192_BE_f64", None, rlbm.RLBM_F64, 4),
              ("fourier_x64_1024x256_FD_bf16dev", W.batched_fourier(), rlbm.RLBM_BF16DEV, 50),
              ("fourier_x64_1024x256_FD_f16dev", None, rlbm.RLBM_F16DEV, 50),
-             ("fourier_x64_1024x256_FD_f32dev", None, rlbm.RLBM_F32DEV, 50)]
+             ("fourier_x64_1024x256_FD_f32dev", None, rlbm.RLBM_F32DEV, 50),
+             ("batched_taylor_green_x256_MJ_bf16dev", W.batched_taylor_green(), rlbm.RLBM_BF16DEV, 50)]
     wl = None
     for name, w, storage, k in cases:
         wl = w if w is not None else wl

@@ -34,7 +34,11 @@ static __constant__ float c_Qf[3][126] = {RLBM_QF_MJ_INIT, RLBM_QF_FD_INIT, RLBM
 static __constant__ float c_Ef[3][18] = {RLBM_EF_MJ_INIT, RLBM_EF_FD_INIT, RLBM_EF_BE_INIT};
 static __constant__ float c_p2f[3][6];
 static __constant__ float c_pnkf[63];
-constexpr int kSerF = 16, kExpBEf = 16, kExpFDf = 26;
+// terms of the power series of Li_nu(x), |x| <= 1/4
+#ifndef RLBM_SERIES_TERMS
+#define RLBM_SERIES_TERMS 12  // the first term left out is below 2^-24 of g_1 for |x| <= 1/4
+#endif
+constexpr int kSerF = RLBM_SERIES_TERMS, kExpBEf = 16, kExpFDf = 26;
 static __constant__ float c_invpowf[6 * kSerF];
 static __constant__ float c_be_expf[6 * kExpBEf];
 static __constant__ float c_fd_expf[6 * kExpFDf];
@@ -56,20 +60,15 @@ constexpr float kRZCf = (float)RLBM_R_ZC;
 constexpr float kZCf = 0.9999999f;
 
 // --------------------------------------------------- FP32 EDF integrals g_nu
-// 1: the series loop fully unrolled, its coefficients immediate constant
-// operands; 4: unrolled by four, coefficients loaded per term
-#ifndef RLBM_SERIES_UNROLL
-#define RLBM_SERIES_UNROLL 4
-#endif
+// sum_{k>=1} x^k k^{-nu}, nu = 1..6, |x| <= 1/4. Fully unrolled, so that the
+// coefficients are immediate constant operands: with the loop rolled, each term
+// loaded its six coefficients first, and the FD and BE steps ran 14 % and 5 %
+// slower.
 __device__ __forceinline__ void li_series6f(float x, float g[6]) {
   float xk = 1.0f;
 #pragma unroll
   for (int i = 0; i < 6; ++i) g[i] = 0.0f;
-#if RLBM_SERIES_UNROLL == 1
 #pragma unroll
-#else
-#pragma unroll 4
-#endif
   for (int k = 1; k <= kSerF; ++k) {
     xk *= x;
 #pragma unroll
@@ -137,13 +136,40 @@ __device__ void g_allf(float z, float g[6]) {
   g[5] = g[5] + fmaf(L6, 1.0f / 720.0f, fmaf(eta2 / 12.0f, L4, fmaf(eta4, L2, 2.0f * eta6)));
 }
 
+// g_1, g_2, g_3 alone (g[0..2] of g_allf), what the Newton iterations below
+// need: in the series range three series instead of six.
+template <int EDF>
+__device__ __forceinline__ void g123f(float z, float g[3]) {
+  if (EDF != EDF_MJ && z <= 0.25f) {
+    const float x = EDF == EDF_BE ? z : -z;
+    float xk = 1.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+#pragma unroll
+    for (int k = 1; k <= kSerF; ++k) {
+      xk *= x;
+      s1 = fmaf(xk, c_invpowf[k - 1], s1);
+      s2 = fmaf(xk, c_invpowf[kSerF + k - 1], s2);
+      s3 = fmaf(xk, c_invpowf[2 * kSerF + k - 1], s3);
+    }
+    const float sg = EDF == EDF_BE ? 1.0f : -1.0f;
+    g[0] = sg * s1;
+    g[1] = sg * s2;
+    g[2] = sg * s3;
+    return;
+  }
+  float g6[6];
+  g_allf<EDF>(z, g6);
+  g[0] = g6[0];
+  g[1] = g6[1];
+  g[2] = g6[2];
+}
+
 // Fugacity from g_3^2/g_2^3 = target (Eq. 25), FP32 safeguarded Newton in mu = ln z.
-// Start: with w = 1/target, the series g_nu = z -+ z^2/2^nu + z^3/3^nu + ... gives
-// ln(1/target) = mu + s z/2 + c z^2 + O(z^3), s = -1 (FD) or +1 (BE),
-// c = 2/27 - 1/64 - 1/3 + 3/32, so mu = ln w - s w/2 + (1/4 - c) w^2 + O(w^3) for
-// small w; two Newton steps then reach the FP32 floor. On convergence the g of
-// the last evaluation is kept with its own z (its mu is within the last step,
-// < 4e-7, of the root).
+// Start: the series g_nu = z + s z^2/2^nu + z^3/3^nu + s z^4/4^nu ... (s = -1 FD,
+// +1 BE) make w = 1/target = g_2^3/g_3^2 a power series in z; inverting it gives
+// mu = ln w - s w/2 + (119/1728) w^2 - s (85/6912) w^3 + O(w^4), off by 1.4e-6 in
+// mu at z = 0.17, so one Newton step reaches the FP32 floor and the next confirms
+// it. The iterations evaluate g_1..g_3 alone; all six g_nu are evaluated once, at
+// the converged mu (the last step applied).
 template <int EDF>
 __device__ int solve_z_R_f(float target, float& z, float g[6]) {
   if (EDF == EDF_BE && target < kRZCf) {
@@ -159,31 +185,30 @@ __device__ int solve_z_R_f(float target, float& z, float g[6]) {
     const float w = 1.0f / target;
     if (w < 0.5f) {
       constexpr float kS = EDF == EDF_BE ? 1.0f : -1.0f;
-      constexpr float kC2 = 0.25f - (2.0f / 27.0f - 1.0f / 64.0f - 1.0f / 3.0f + 3.0f / 32.0f);
-      mu = fmaf(fmaf(kC2, w, -0.5f * kS), w, mu);
+      mu = fmaf(fmaf(fmaf(-kS * (85.0f / 6912.0f), w, 119.0f / 1728.0f), w, -0.5f * kS), w, mu);
     }
   }
   mu = fminf(fmaxf(mu, lo + 1e-3f), hi);
   int st = ST_ZSOLVE;
   float dprev = INFINITY;
   for (int it = 0; it < 40; ++it) {
-    const float ze = expf(mu);
-    g_allf<EDF>(ze, g);
-    const float F = logf(g[2] * g[2] / (g[1] * g[1] * g[1])) - lt;
+    float gi[3];
+    g123f<EDF>(expf(mu), gi);
+    const float F = logf(gi[2] * gi[2] / (gi[1] * gi[1] * gi[1])) - lt;
     if (F == 0.0f) {
-      z = ze;
-      return 0;
+      st = 0;
+      break;
     }
-    const float dF = 2.0f * g[1] / g[2] - 3.0f * g[0] / g[1];
+    const float dF = 2.0f * gi[1] / gi[2] - 3.0f * gi[0] / gi[1];
     if (F > 0.0f) lo = mu; else hi = mu;
     float mn = mu - F / dF;
     if (!(mn >= lo && mn <= hi)) mn = 0.5f * (lo + hi);
     const float d = fabsf(mn - mu);
-    if (d <= 4e-7f * fmaxf(1.0f, fabsf(mn)) || (d < 1e-4f && d >= dprev)) {
-      z = ze;
-      return 0;
-    }
     mu = mn;
+    if (d <= 4e-7f * fmaxf(1.0f, fabsf(mu)) || (d < 1e-4f && d >= dprev)) {
+      st = 0;
+      break;
+    }
     dprev = d;
   }
   z = expf(mu);
@@ -191,7 +216,10 @@ __device__ int solve_z_R_f(float target, float& z, float g[6]) {
   return st;
 }
 
-// Fugacity from (n, theta): n = 2 pi theta^2 g_2(z), FP32.
+// Fugacity from (n, theta): n = 2 pi theta^2 g_2(z), FP32 safeguarded Newton in
+// mu = ln z. Start: inverting G = g_2(z) = z -+ z^2/4 + z^3/9 -+ ... (G = n / (2 pi
+// theta^2)) gives mu = ln G +- G/4 - (5/288) G^2 +- G^3/288 + O(G^4) (upper signs
+// FD, lower BE) for small G. Convergence as in solve_z_R_f.
 template <int EDF>
 __device__ int solve_z_nt_f(float n, float theta, float& z, float g[6]) {
   const float G = n / (2.0f * kPIf * theta * theta);
@@ -208,20 +236,32 @@ __device__ int solve_z_nt_f(float n, float theta, float& z, float g[6]) {
   }
   float lo = -40.0f, hi = (EDF == EDF_BE) ? -1.0e-7f : 40.0f;
   const float lG = logf(G);
-  float mu = fminf(fmaxf(lG, lo + 1e-3f), hi);
-  int st = ST_ZSOLVE;
+  float mu = lG;
+  if (G < 0.5f) {
+    constexpr float kS = EDF == EDF_BE ? -1.0f : 1.0f;
+    mu = fmaf(fmaf(fmaf(kS / 288.0f, G, -5.0f / 288.0f), G, 0.25f * kS), G, mu);
+  }
+  mu = fminf(fmaxf(mu, lo + 1e-3f), hi);
   float dprev = INFINITY;
+  int st = ST_ZSOLVE;
   for (int it = 0; it < 40; ++it) {
-    g_allf<EDF>(expf(mu), g);
-    const float F = logf(g[1]) - lG;
-    if (F == 0.0f) { st = 0; break; }
-    const float dF = g[0] / g[1];
+    float gi[3];
+    g123f<EDF>(expf(mu), gi);
+    const float F = logf(gi[1]) - lG;
+    if (F == 0.0f) {
+      st = 0;
+      break;
+    }
+    const float dF = gi[0] / gi[1];
     if (F < 0.0f) lo = mu; else hi = mu;
     float mn = mu - F / dF;
     if (!(mn >= lo && mn <= hi)) mn = 0.5f * (lo + hi);
     const float d = fabsf(mn - mu);
     mu = mn;
-    if (d <= 4e-7f * fmaxf(1.0f, fabsf(mu)) || (d < 1e-4f && d >= dprev)) { st = 0; break; }
+    if (d <= 4e-7f * fmaxf(1.0f, fabsf(mu)) || (d < 1e-4f && d >= dprev)) {
+      st = 0;
+      break;
+    }
     dprev = d;
   }
   z = expf(mu);
@@ -414,9 +454,11 @@ __device__ __noinline__ void write_halo_mixed(const DomDev& D, int x, int y, typ
 constexpr size_t kSmemF = 72 * kThreads * sizeof(float);  // the shared-memory column of a block
 
 #ifndef RLBM_MIXED_MIN_BLOCKS
-// resident blocks per SM the register budget must allow: 512 threads (128
-// registers), measured fastest on the 2048^2 FP32-deviation case
-#define RLBM_MIXED_MIN_BLOCKS (512 / kThreads)
+// resident blocks per SM the register budget must allow: 640 threads (96
+// registers, no spills; 20 warps per SM). Measured against 512 threads (128
+// registers) and 768 (80 registers, spills): 2 % faster than the first on every
+// workload, 12 % faster than the second.
+#define RLBM_MIXED_MIN_BLOCKS (640 / kThreads)
 #endif
 // 1: at the start of a tile one thread asks L2 for the tile's own blocks in rows
 // y0-1 .. y0+kTileH (one contiguous segment per row), so that the pull's later
