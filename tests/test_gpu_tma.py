@@ -51,9 +51,14 @@ def test_tma_matches_l1_bitwise(R, edf, stname):
     assert np.array_equal(a[0], b[0])
 
 
-@pytest.mark.parametrize("nx", [1, 2, 3, 31, 33, 63])
+@pytest.mark.parametrize("nx", [1, 2, 3, 16, 17, 31, 33, 48, 63])
 def test_tma_matches_l1_on_narrow_and_ragged_widths(R, nx):
-    specs = [W.DomainSpec(nx, 9, 0.9, 0), W.DomainSpec(nx, 6, 1.2, 0, (1, 1, 2, 2), (1.0, 1.0, 0.98, 1.02))]
+    """The L1 step walks packed tiles (a last block of w <= 16 cells, 32/w rows per
+    warp) and wraps across periodic sides; the TMA step walks 32 x 4 tiles and
+    reads the stored halo images: w = 1, 2, 3, 16 packed, 17 and 31 not, and
+    periodic x with walls in y, zero-gradient x with walls, periodic both ways."""
+    specs = [W.DomainSpec(nx, 9, 0.9, 0), W.DomainSpec(nx, 6, 1.2, 0, (1, 1, 2, 2), (1.0, 1.0, 0.98, 1.02)),
+             W.DomainSpec(nx, 13, 0.8, 0, (0, 0, 2, 2), (1.0, 1.0, 1.03, 0.97))]
     inits = [W.random_domain_state(nx, s.ny, 60 + i) for i, s in enumerate(specs)]
     a, _ = _populations(R, specs, inits, 4, R.RLBM_KERNEL_L1, 7)
     b, st = _populations(R, specs, inits, 4, R.RLBM_KERNEL_TMA, 7)
