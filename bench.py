@@ -552,7 +552,7 @@ def run_reference(args):
     sample_txt = "first %d domains of %s (%d cells), full step each" % (len(sample), wl.name, cells)
     line = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t / args.steps * 1e3, 2),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": args.scaling, "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
             "config": {"workload": wl.name, "sample": sample_txt},
             "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": O.num_threads(),
