@@ -174,7 +174,8 @@ int rlbm_moments_all(rlbm_handle h, int streamed, double *n, double *theta, doub
 int rlbm_diagnostics(rlbm_handle h, int domain, int streamed, double *out, int on_device);
 
 /* Raw state of domain `domain` for checkpoint/resume: the stored populations
- * including the one-cell halo ring, as FP64 [72][ny+2][nx+2] (index
+ * including the one-cell halo ring (periodic images, which the mixed L1 step
+ * does not store, are filled from the interior first), as FP64 [72][ny+2][nx+2] (index
  * (q*(ny+2) + y+1)*(nx+2) + x+1 for x in -1..nx, y in -1..ny), converted from
  * the storage format. rlbm_set_populations writes them back (rounded to the
  * storage format); a resumed run then continues bit-for-bit. */

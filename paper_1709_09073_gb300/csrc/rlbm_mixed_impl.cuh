@@ -499,16 +499,18 @@ __device__ __forceinline__ void relax_cell(const DomDev& D, const float zr[21], 
 // each direction; stores f* to fout, writes the cell's halo images and returns
 // its status bits. Called by the active lanes of a warp (the lanes of cells
 // inside the domain). kImages: also write the periodic halo images (the
-// TMA-staged step reads them; the L1 pull wraps instead).
-template <int EDF, class S, bool kImages>
+// TMA-staged step reads them; the L1 pull wraps instead). kHalo = false: no
+// domain of the launch has a non-periodic side, so with kImages = false there is
+// no halo cell to write and the relaxed values need not go back to the column.
+template <int EDF, class S, bool kImages, bool kHalo = true>
 __device__ __forceinline__ unsigned collide_mixed(const DomDev& D, int x, int y, long long c, const float A[12],
                                                   const float B[12], float* smf, int tid,
                                                   typename S::T* __restrict__ fout) {
   // a warp with no cell on an edge that has halo cells to write skips the halo
   // writer (uniform per warp)
   const bool edge = kImages ? (x == 0 || x == D.nx - 1 || y == 0 || y == D.ny - 1)
-                            : (D.bc[0] != BC_PERIODIC && (x == 0 || x == D.nx - 1)) ||
-                                  (D.bc[2] != BC_PERIODIC && (y == 0 || y == D.ny - 1));
+                            : kHalo && ((D.bc[0] != BC_PERIODIC && (x == 0 || x == D.nx - 1)) ||
+                                        (D.bc[2] != BC_PERIODIC && (y == 0 || y == D.ny - 1)));
   const bool edge_warp = __any_sync(__activemask(), edge);
   const HarmF ha = harmonics_f(A), hb = harmonics_f(B);
   // moment totals in double-float: reference moments + FP32 deviation sums
@@ -587,16 +589,21 @@ __device__ __forceinline__ unsigned collide_mixed(const DomDev& D, int x, int y,
     float om[12];
 #pragma unroll
     for (int d = 0; d < 12; ++d) om[d] = relax_rate(d, gf, uxf, uyf, itau);
+    if constexpr (!kImages && !kHalo) {
+      relax_cell<EDF, S, false>(D, zr, zi, om, smf, tid, c, fout);
+    } else {
 #if RLBM_MIXED_EDGE_WARPS
-    if (edge_warp) relax_cell<EDF, S, true>(D, zr, zi, om, smf, tid, c, fout);
-    else relax_cell<EDF, S, false>(D, zr, zi, om, smf, tid, c, fout);
+      if (edge_warp) relax_cell<EDF, S, true>(D, zr, zi, om, smf, tid, c, fout);
+      else relax_cell<EDF, S, false>(D, zr, zi, om, smf, tid, c, fout);
 #else
-    relax_cell<EDF, S, true>(D, zr, zi, om, smf, tid, c, fout);
+      relax_cell<EDF, S, true>(D, zr, zi, om, smf, tid, c, fout);
 #endif
+    }
   } else {
     for (int q = 0; q < 72; ++q) fout[q * kBlkW + c] = S::encf(smf[q * kThreads + tid], D, q % 6);
   }
-  if (edge_warp) write_halo_mixed<EDF, S>(D, x, y, fout, smf + tid, ok, nf, uxf, uyf, gf, st, kImages);
+  if (kImages || kHalo)
+    if (edge_warp) write_halo_mixed<EDF, S>(D, x, y, fout, smf + tid, ok, nf, uxf, uyf, gf, st, kImages);
   return st;
 }
 
@@ -615,7 +622,7 @@ __device__ __forceinline__ void prefetch_tile_l2(const DomDev& D, const Tile& tl
 
 // One tile of the step (32 x 4 cells, or a packed ragged block): pull,
 // collide, store (the thread's cell).
-template <int EDF, class S>
+template <int EDF, class S, bool kHalo>
 __device__ __forceinline__ void step_tile_mixed(const StepArgs& a, int t, float* smf, int tid) {
   const Tile tl = a.tiles[t];
   const DomDev& D = a.doms[tl.dom];
@@ -652,16 +659,18 @@ __device__ __forceinline__ void step_tile_mixed(const StepArgs& a, int t, float*
   RLBM_PULL_DIR(4) RLBM_PULL_DIR(5) RLBM_PULL_DIR(6) RLBM_PULL_DIR(7)
   RLBM_PULL_DIR(8) RLBM_PULL_DIR(9) RLBM_PULL_DIR(10) RLBM_PULL_DIR(11)
 #undef RLBM_PULL_DIR
-  const unsigned st = collide_mixed<EDF, S, false>(D, x, y, c, A, B, smf, tid, fout);
+  const unsigned st = collide_mixed<EDF, S, false, kHalo>(D, x, y, c, A, B, smf, tid, fout);
   if (st) atomicOr(a.status, st);
 }
 
-template <int EDF, class S>
+// kHalo = false: every domain of the launch is periodic on all sides (launched
+// when StepArgs::halo is 0): no halo writer and no copy of the relaxed values.
+template <int EDF, class S, bool kHalo>
 __global__ void __launch_bounds__(kThreads, RLBM_MIXED_MIN_BLOCKS) k_step_mixed(StepArgs a) {
   extern __shared__ float smf[];
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
-    step_tile_mixed<EDF, S>(a, t, smf, tid);
+    step_tile_mixed<EDF, S, kHalo>(a, t, smf, tid);
   }
 }
 
@@ -1079,7 +1088,9 @@ template <class S, int EDF>
 static cudaError_t prepare_mixed_t() {
   cudaError_t e = cudaFuncSetAttribute(k_init_mixed<EDF, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemF);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_step_mixed<EDF, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemF);
+  e = cudaFuncSetAttribute(k_step_mixed<EDF, S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemF);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_step_mixed<EDF, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemF);
 }
 
 template <class S>
@@ -1134,10 +1145,19 @@ static cudaError_t step_s(int edf, const StepArgs& a, int grid, cudaStream_t s) 
     }
     return cudaGetLastError();
   }
-  switch (edf) {
-    case EDF_MJ: k_step_mixed<EDF_MJ, S><<<grid, dim3(kTileW, kTileH), kSmemF, s>>>(a); break;
-    case EDF_FD: k_step_mixed<EDF_FD, S><<<grid, dim3(kTileW, kTileH), kSmemF, s>>>(a); break;
-    default: k_step_mixed<EDF_BE, S><<<grid, dim3(kTileW, kTileH), kSmemF, s>>>(a); break;
+  const dim3 blk(kTileW, kTileH);
+  if (a.halo) {
+    switch (edf) {
+      case EDF_MJ: k_step_mixed<EDF_MJ, S, true><<<grid, blk, kSmemF, s>>>(a); break;
+      case EDF_FD: k_step_mixed<EDF_FD, S, true><<<grid, blk, kSmemF, s>>>(a); break;
+      default: k_step_mixed<EDF_BE, S, true><<<grid, blk, kSmemF, s>>>(a); break;
+    }
+  } else {
+    switch (edf) {
+      case EDF_MJ: k_step_mixed<EDF_MJ, S, false><<<grid, blk, kSmemF, s>>>(a); break;
+      case EDF_FD: k_step_mixed<EDF_FD, S, false><<<grid, blk, kSmemF, s>>>(a); break;
+      default: k_step_mixed<EDF_BE, S, false><<<grid, blk, kSmemF, s>>>(a); break;
+    }
   }
   return cudaGetLastError();
 }

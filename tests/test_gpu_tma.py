@@ -150,3 +150,19 @@ def test_copy_wait_limit_runs_out_and_the_handle_recovers(R):
     sim.close()
     assert st2 == s_ref == 0
     assert np.array_equal(out, ref[0])
+
+
+@pytest.mark.parametrize("edf", [0, 1])
+def test_tma_matches_l1_on_a_periodic_batch(R, edf):
+    """A handle whose domains are all periodic launches the L1 step without its
+    halo writer (nothing to write: the pull wraps); the TMA step writes and
+    reads the periodic images. Ragged, packed and one-cell-wide domains."""
+    specs = [W.DomainSpec(37, 11, 0.8, edf), W.DomainSpec(5, 9, 1.1, edf), W.DomainSpec(64, 4, 0.7, edf),
+             W.DomainSpec(1, 3, 0.9, edf), W.DomainSpec(50, 21, 1.6, edf)]
+    inits = [W.random_domain_state(s.nx, s.ny, 70 + i, edf, u_amp=0.05) for i, s in enumerate(specs)]
+    for stname, storage in STORAGES.items():
+        a, _ = _populations(R, specs, inits, storage, R.RLBM_KERNEL_L1, 9)
+        b, st = _populations(R, specs, inits, storage, R.RLBM_KERNEL_TMA, 9)
+        assert st == 0, stname
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y), stname
