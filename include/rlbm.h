@@ -68,8 +68,18 @@ typedef enum { RLBM_F64 = 0, RLBM_F32 = 1, RLBM_BF16DEV = 2, RLBM_F16DEV = 3, RL
  *                      f* - f^eq of the adjacent fluid cell's last collision
  *                      (non-equilibrium extrapolation). FP64 storage only; all such
  *                      sides of a domain share one theta_wall.
+ *  RLBM_EXCHANGED      y sides only: the ghost row is supplied by the caller
+ *                      (rlbm_unpack_ghost_rows, the face of a neighbouring y-slab)
+ *                      and the library never writes it. It must be supplied
+ *                      before every step and before a streamed read-out.
  *  At a corner outside both axes an x-side wall takes precedence over a y-side wall. */
-typedef enum { RLBM_PERIODIC = 0, RLBM_ZERO_GRADIENT = 1, RLBM_FIXED_T_WALL = 2, RLBM_VELOCITY_WALL = 3 } rlbm_bc;
+typedef enum {
+  RLBM_PERIODIC = 0,
+  RLBM_ZERO_GRADIENT = 1,
+  RLBM_FIXED_T_WALL = 2,
+  RLBM_VELOCITY_WALL = 3,
+  RLBM_EXCHANGED = 4
+} rlbm_bc;
 
 /* Meaning of the first field given to rlbm_init. */
 typedef enum { RLBM_INIT_N_THETA = 0, RLBM_INIT_Z_THETA = 1 } rlbm_init_kind;
@@ -297,7 +307,8 @@ int rlbm_last_step_info(rlbm_handle h, long long *cell_updates, int *kernel_laun
  * RLBM_F64) without a handle or workspace and without allocating anything:
  * no cudaMalloc, cudaFree or allocating library routine is called.
  *  - domain: host descriptor, checked as rlbm_create checks it (ref_n,
- *    ref_theta, scale ignored; eta_s > 0 selects the local tau); edf: rlbm_edf.
+ *    ref_theta, scale ignored; eta_s > 0 selects the local tau; RLBM_EXCHANGED
+ *    sides are refused, having no face to receive); edf: rlbm_edf.
  *  - f_in, f_out: caller-owned DEVICE buffers, FP64 [72][ny+2][nx+2] with the
  *    halo ring -- the layout of rlbm_get_populations -- holding the stored
  *    post-collision populations before and after the steps. The halo of f_in

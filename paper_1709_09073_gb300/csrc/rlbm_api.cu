@@ -43,7 +43,8 @@ struct Layout {
 };
 
 bool valid_bc(int b) {
-  return b == RLBM_PERIODIC || b == RLBM_ZERO_GRADIENT || b == RLBM_FIXED_T_WALL || b == RLBM_VELOCITY_WALL;
+  return b == RLBM_PERIODIC || b == RLBM_ZERO_GRADIENT || b == RLBM_FIXED_T_WALL || b == RLBM_VELOCITY_WALL ||
+         b == RLBM_EXCHANGED;
 }
 
 int validate(const rlbm_config* c) {
@@ -57,6 +58,8 @@ int validate(const rlbm_config* c) {
     if (!(d.eta_s >= 0.0) || !(d.eta_s < 1e300)) return RLBM_E_ARG;
     if (!valid_bc(d.bc_xlo) || !valid_bc(d.bc_xhi) || !valid_bc(d.bc_ylo) || !valid_bc(d.bc_yhi))
       return RLBM_E_ARG;
+    // faces are exchanged along y only (rlbm_pack_edge_rows / rlbm_unpack_ghost_rows)
+    if (d.bc_xlo == RLBM_EXCHANGED || d.bc_xhi == RLBM_EXCHANGED) return RLBM_E_ARG;
     if ((d.bc_xlo == RLBM_PERIODIC) != (d.bc_xhi == RLBM_PERIODIC)) return RLBM_E_ARG;
     if ((d.bc_ylo == RLBM_PERIODIC) != (d.bc_yhi == RLBM_PERIODIC)) return RLBM_E_ARG;
     const double tw[4] = {d.t_wall_xlo, d.t_wall_xhi, d.t_wall_ylo, d.t_wall_yhi};
@@ -427,7 +430,8 @@ int rlbm_create(const rlbm_config* c, rlbm_handle* out) {
   h->any_halo = 0;
   for (const rlbm_domain& d : h->doms) {
     h->cells += (long long)d.nx * d.ny;
-    if (d.bc_xlo != RLBM_PERIODIC || d.bc_ylo != RLBM_PERIODIC) h->any_halo = 1;
+    for (int b : {d.bc_xlo, d.bc_xhi, d.bc_ylo, d.bc_yhi})
+      if (bc_writes_halo(b)) h->any_halo = 1;
   }
   h->base = static_cast<char*>(c->device_buffer);
   h->d_status = reinterpret_cast<unsigned*>(h->base + h->L.status_off);

@@ -6,7 +6,12 @@
 namespace rlbm {
 
 enum { EDF_MJ = 0, EDF_FD = 1, EDF_BE = 2 };
-enum { BC_PERIODIC = 0, BC_ZERO_GRADIENT = 1, BC_WALL = 2, BC_VWALL = 3 };
+enum { BC_PERIODIC = 0, BC_ZERO_GRADIENT = 1, BC_WALL = 2, BC_VWALL = 3, BC_EXCHANGED = 4 };
+// a side whose ghost is an equilibrium (fixed-T or velocity wall)
+__host__ __device__ inline bool bc_is_wall(int b) { return b == BC_WALL || b == BC_VWALL; }
+// a side whose ghost the step writes (not periodic: the pull wraps; not
+// exchanged: the caller supplies it)
+__host__ __device__ inline bool bc_writes_halo(int b) { return b != BC_PERIODIC && b != BC_EXCHANGED; }
 enum { ST_F64 = 0, ST_F32 = 1, ST_BF16DEV = 2, ST_F16DEV = 3, ST_F32DEV = 4 };
 
 // per-cell status bits (identical to the public RLBM_W_* values)

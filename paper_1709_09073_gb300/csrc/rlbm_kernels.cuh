@@ -205,8 +205,9 @@ __device__ __forceinline__ int halo_targets(const DomDev& D, int x, int y, int h
     if (images && y == ny - 1) ys[nY++] = -1;
     if (images && y == 0) ys[nY++] = ny;
   } else {
-    if (y == 0) ys[nY++] = -1;
-    if (y == ny - 1) ys[nY++] = ny;
+    // an exchanged side's ghost row is the neighbour's face: nothing to write
+    if (y == 0 && D.bc[2] != BC_EXCHANGED) ys[nY++] = -1;
+    if (y == ny - 1 && D.bc[3] != BC_EXCHANGED) ys[nY++] = ny;
   }
   int cnt = 0;
   for (int i = 0; i < nX; ++i)
@@ -214,10 +215,10 @@ __device__ __forceinline__ int halo_targets(const DomDev& D, int x, int y, int h
       if (i == 0 && j == 0) continue;
       const int tx = xs[i], ty = ys[j];
       int w = -1;
-      if (tx == -1 && D.bc[0] >= BC_WALL) w = 0;
-      else if (tx == nx && D.bc[1] >= BC_WALL) w = 1;
-      else if (ty == -1 && D.bc[2] >= BC_WALL) w = 2;
-      else if (ty == ny && D.bc[3] >= BC_WALL) w = 3;
+      if (tx == -1 && bc_is_wall(D.bc[0])) w = 0;
+      else if (tx == nx && bc_is_wall(D.bc[1])) w = 1;
+      else if (ty == -1 && bc_is_wall(D.bc[2])) w = 2;
+      else if (ty == ny && bc_is_wall(D.bc[3])) w = 3;
       hx[cnt] = tx;
       hy[cnt] = ty;
       wall[cnt] = w;

@@ -509,8 +509,10 @@ __device__ __forceinline__ unsigned collide_mixed(const DomDev& D, int x, int y,
   // a warp with no cell on an edge that has halo cells to write skips the halo
   // writer (uniform per warp)
   const bool edge = kImages ? (x == 0 || x == D.nx - 1 || y == 0 || y == D.ny - 1)
-                            : kHalo && ((D.bc[0] != BC_PERIODIC && (x == 0 || x == D.nx - 1)) ||
-                                        (D.bc[2] != BC_PERIODIC && (y == 0 || y == D.ny - 1)));
+                            : kHalo && ((x == 0 && bc_writes_halo(D.bc[0])) ||
+                                        (x == D.nx - 1 && bc_writes_halo(D.bc[1])) ||
+                                        (y == 0 && bc_writes_halo(D.bc[2])) ||
+                                        (y == D.ny - 1 && bc_writes_halo(D.bc[3])));
   const bool edge_warp = __any_sync(__activemask(), edge);
   const HarmF ha = harmonics_f(A), hb = harmonics_f(B);
   // moment totals in double-float: reference moments + FP32 deviation sums

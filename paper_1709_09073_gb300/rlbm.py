@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "librlbm.so")
 
 RLBM_MJ, RLBM_FD, RLBM_BE = 0, 1, 2
 RLBM_F64, RLBM_F32, RLBM_BF16DEV, RLBM_F16DEV, RLBM_F32DEV = 0, 1, 2, 3, 4
-RLBM_PERIODIC, RLBM_ZERO_GRADIENT, RLBM_FIXED_T_WALL, RLBM_VELOCITY_WALL = 0, 1, 2, 3
+RLBM_PERIODIC, RLBM_ZERO_GRADIENT, RLBM_FIXED_T_WALL, RLBM_VELOCITY_WALL, RLBM_EXCHANGED = 0, 1, 2, 3, 4
 RLBM_INIT_N_THETA, RLBM_INIT_Z_THETA = 0, 1
 RLBM_OK = 0
 RLBM_W_LANDAU_MAXITER, RLBM_W_CLAMPED_FUGACITY, RLBM_W_NONPHYSICAL, RLBM_W_ZSOLVE = 1, 2, 4, 8

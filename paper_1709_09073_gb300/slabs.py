@@ -61,17 +61,21 @@ def neighbours(rank, nranks, periodic_y):
     return below, above
 
 
-def slab_bcs(bc, rank, nranks):
+ZERO_GRADIENT, EXCHANGED = 1, 4
+
+
+def slab_bcs(bc, rank, nranks, internal=EXCHANGED):
     """Boundary conditions of a slab: x sides as the domain's; a y side that
-    borders another slab gets zero-gradient, a placeholder never read because
-    that row is supplied by the neighbour. A single slab is the whole domain."""
+    borders another slab gets `internal`. EXCHANGED (the device path) has the
+    step write nothing there, since the neighbour's face fills that ghost row;
+    ZERO_GRADIENT (the oracle, which knows no exchanged side) is a placeholder
+    that the face overwrites. A single slab is the whole domain."""
     if nranks == 1:
         return tuple(bc)
     xlo, xhi, ylo, yhi = bc
     periodic_y = ylo == 0
-    ZG = 1
-    lo = ZG if (periodic_y or rank > 0) else ylo
-    hi = ZG if (periodic_y or rank < nranks - 1) else yhi
+    lo = internal if (periodic_y or rank > 0) else ylo
+    hi = internal if (periodic_y or rank < nranks - 1) else yhi
     return (xlo, xhi, lo, hi)
 
 

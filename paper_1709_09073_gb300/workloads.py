@@ -11,7 +11,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 MJ, FD, BE = 0, 1, 2
-PERIODIC, ZERO_GRADIENT, FIXED_T_WALL, VELOCITY_WALL = 0, 1, 2, 3
+PERIODIC, ZERO_GRADIENT, FIXED_T_WALL, VELOCITY_WALL, EXCHANGED = 0, 1, 2, 3, 4
 INIT_N_THETA, INIT_Z_THETA = 0, 1
 Z_C = 1.0 - 1.0e-7  # BE reference fugacity, Eq. (15)
 

@@ -84,6 +84,11 @@ def test_workspace_sizing_and_validation(lib_path):
     assert rlbm.rlbm_workspace_bytes([W.DomainSpec(4, 8, 3.0, accel=(1e-8, 0.0))], 0, rlbm.RLBM_F32DEV) == 0
     assert rlbm.rlbm_workspace_bytes([W.DomainSpec(4, 8, 3.0, bc=vw, t_wall=(1, 1, 1.0, 1.1))], 0, 0) == 0
     assert rlbm.rlbm_workspace_bytes([W.DomainSpec(4, 8, 3.0, bc=vw, n_wall=0.0)], 0, 0) == 0
+    # exchanged sides (a y-slab's faces): y sides only, never paired with a periodic side
+    ex = (W.PERIODIC, W.PERIODIC, W.EXCHANGED, W.FIXED_T_WALL)
+    assert rlbm.rlbm_workspace_bytes([W.DomainSpec(8, 4, 0.9, bc=ex, t_wall=(1, 1, 1, 1.02))], 0, 0) > 0
+    assert rlbm.rlbm_workspace_bytes([W.DomainSpec(8, 4, 0.9, bc=(W.EXCHANGED, 1, 0, 0))], 0, 0) == 0
+    assert rlbm.rlbm_workspace_bytes([W.DomainSpec(8, 4, 0.9, bc=(0, 0, W.EXCHANGED, 0))], 0, 0) == 0
 
 
 def test_struct_layout_matches_header():

@@ -1,7 +1,8 @@
 """Device y-slabs (rlbm_pack_edge_rows / rlbm_unpack_ghost_rows and
 slabs.DeviceSlab): one domain cut into uneven y-slabs, each fed every step
 only the 30 edge-row planes its neighbours send (Eqs. 17-18: the pull reaches
-one row), reproduces the undivided domain on the GPU bit for bit -- stored
+one row) into the ghost row of an RLBM_EXCHANGED side (or of a zero-gradient
+placeholder side), reproduces the undivided domain on the GPU bit for bit -- stored
 populations and streamed fields -- in every storage format and in both step
 kernels, with periodic, fixed-temperature-wall, zero-gradient and
 velocity-wall sides and a body force. In process the slabs are domains of one
@@ -35,9 +36,9 @@ def R():
     return rlbm
 
 
-def _slab_specs(spec, bounds):
+def _slab_specs(spec, bounds, internal=slabs.EXCHANGED):
     n = len(bounds)
-    return [dataclasses.replace(spec, ny=y1 - y0, bc=slabs.slab_bcs(spec.bc, r, n))
+    return [dataclasses.replace(spec, ny=y1 - y0, bc=slabs.slab_bcs(spec.bc, r, n, internal))
             for r, (y0, y1) in enumerate(bounds)]
 
 
@@ -82,8 +83,8 @@ def _whole(R, spec, init, steps, storage, kernel):
     return f, out, st
 
 
-def _slabbed(R, spec, init, bounds, steps, storage, kernel):
-    specs = _slab_specs(spec, bounds)
+def _slabbed(R, spec, init, bounds, steps, storage, kernel, internal=slabs.EXCHANGED):
+    specs = _slab_specs(spec, bounds, internal)
     sim = R.Simulation(specs, edf=spec.edf, storage=storage)
     st = 0
     for r, (y0, y1) in enumerate(bounds):
@@ -117,9 +118,9 @@ CASES = {
 }
 
 
-def _check_equal(R, spec, init, bounds, steps, storage, kernel=None):
+def _check_equal(R, spec, init, bounds, steps, storage, kernel=None, internal=slabs.EXCHANGED):
     f0, out0, st0 = _whole(R, spec, init, steps, storage, kernel)
-    f1, out1, st1 = _slabbed(R, spec, init, bounds, steps, storage, kernel)
+    f1, out1, st1 = _slabbed(R, spec, init, bounds, steps, storage, kernel, internal)
     assert (st0 & R.RLBM_W_NONPHYSICAL) == 0 and st0 == st1
     assert np.array_equal(f1, f0[:, 1:-1, :])
     for k in range(5):
@@ -158,6 +159,20 @@ def test_mixed_storage_slabs_bit_exact(R, storage, name):
     spec = W.DomainSpec(nx, ny, 0.8, W.MJ, bc, tw, scale=0.5)
     init = W.random_domain_state(nx, ny, 43, W.MJ, u_amp=0.05)
     _check_equal(R, spec, init, [(0, 6), (6, 7), (7, 14)], 10, getattr(R, storage))
+
+
+@pytest.mark.parametrize("storage", ["RLBM_F64", "RLBM_F32DEV"])
+@pytest.mark.parametrize("name", ["periodic", "x_walls", "channel_force"])
+def test_zero_gradient_placeholder_slabs_bit_exact(R, storage, name):
+    """The slab sides facing a neighbour as zero-gradient placeholders (the
+    step writes copies there, which the next face overwrites) instead of
+    RLBM_EXCHANGED sides: the same populations and fields."""
+    if name == "channel_force" and storage != "RLBM_F64":
+        pytest.skip("velocity walls are FP64 only")
+    bc, tw, extra = CASES[name]
+    spec = W.DomainSpec(31, 12, 0.85, W.MJ, bc, tw, **extra)
+    init = W.random_domain_state(31, 12, 47, W.MJ, u_amp=0.05)
+    _check_equal(R, spec, init, [(0, 5), (5, 12)], 8, getattr(R, storage), internal=slabs.ZERO_GRADIENT)
 
 
 @pytest.mark.parametrize("storage", ["RLBM_F32DEV", "RLBM_F16DEV"])

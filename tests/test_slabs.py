@@ -44,9 +44,10 @@ def test_plan():
     assert slabs.neighbours(0, 2, True) == (1, 1)
     assert slabs.neighbours(0, 1, True) == (None, None)
     assert slabs.slab_bcs((0, 0, 0, 0), 0, 1) == (0, 0, 0, 0)
-    assert slabs.slab_bcs((0, 0, 0, 0), 0, 2) == (0, 0, 1, 1)
-    assert slabs.slab_bcs((2, 2, 2, 2), 1, 3) == (2, 2, 1, 1)
-    assert slabs.slab_bcs((2, 2, 2, 2), 2, 3) == (2, 2, 1, 2)
+    assert slabs.slab_bcs((0, 0, 0, 0), 0, 2) == (0, 0, 4, 4)
+    assert slabs.slab_bcs((2, 2, 2, 2), 1, 3) == (2, 2, 4, 4)
+    assert slabs.slab_bcs((2, 2, 2, 2), 2, 3) == (2, 2, 4, 2)
+    assert slabs.slab_bcs((2, 2, 2, 2), 2, 3, internal=1) == (2, 2, 1, 2)
     with pytest.raises(ValueError):
         slabs.slab_bounds(2, 3)
 
@@ -75,7 +76,7 @@ class _Slab:
         self.orc = orc
         y0, y1 = slabs.slab_bounds(spec.ny, nranks)[rank]
         self.y0, self.y1 = y0, y1
-        bc = slabs.slab_bcs(spec.bc, rank, nranks)
+        bc = slabs.slab_bcs(spec.bc, rank, nranks, internal=slabs.ZERO_GRADIENT)
         self.dom = _domain(orc, spec, y1 - y0, bc)
         cut = lambda a: np.ascontiguousarray(a[y0:y1])
         self.f, self.m, _ = orc.init(self.dom, init.kind, cut(init.a), cut(init.theta), cut(init.ux),
