@@ -182,7 +182,7 @@ struct rlbm_ctx {
   int kernel = RLBM_KERNEL_L1;   // mixed step variant (rlbm_select_kernel)
   unsigned long long wait_ns = 0;  // TMA copy-wait limit (0: the default, rlbm_set_wait_limit)
   bool images_stale = false;     // the current copy lacks its periodic halo images (fill_images)
-  int any_halo = 1;              // some domain has a non-periodic side
+  int any_halo = 1;              // some domain has a side whose ghosts the step writes
 };
 
 namespace {
@@ -639,7 +639,7 @@ int rlbm_init_all(rlbm_handle h, int kind, const double* a, const double* theta,
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return RLBM_E_CUDA;
   for (char& v : h->initialized) v = 1;
-  h->images_stale = false;  // the initialisers write every halo cell
+  h->images_stale = false;  // the initialisers write the periodic images too
   return (int)st;
 }
 

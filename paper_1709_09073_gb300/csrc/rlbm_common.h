@@ -106,7 +106,7 @@ struct StepArgs {
   unsigned* status;       // OR of per-cell status bits
   const void* tmaps;      // TMA load descriptors of fin, one per domain (kTensorMapBytes each), or null
   int variant;            // mixed step kernel (RLBM_KERNEL_*); the FP64 step has one
-  int halo;               // some domain has a non-periodic side (halo cells to write)
+  int halo;               // some domain has a side whose ghosts the step writes (bc_writes_halo)
   unsigned long long wait_ns;  // limit of the TMA variant's copy waits (0: kDefaultWaitNs)
 };
 

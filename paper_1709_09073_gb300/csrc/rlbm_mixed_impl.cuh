@@ -61,9 +61,8 @@ constexpr float kZCf = 0.9999999f;
 
 // --------------------------------------------------- FP32 EDF integrals g_nu
 // sum_{k>=1} x^k k^{-nu}, nu = 1..6, |x| <= 1/4. Fully unrolled, so that the
-// coefficients are immediate constant operands: with the loop rolled, each term
-// loaded its six coefficients first, and the FD and BE steps ran 14 % and 5 %
-// slower.
+// coefficients are immediate constant operands. Rolled, each term loaded its
+// six coefficients first; unrolling made the FD and BE steps 14 % and 5 % faster.
 __device__ __forceinline__ void li_series6f(float x, float g[6]) {
   float xk = 1.0f;
 #pragma unroll
@@ -500,8 +499,9 @@ __device__ __forceinline__ void relax_cell(const DomDev& D, const float zr[21], 
 // its status bits. Called by the active lanes of a warp (the lanes of cells
 // inside the domain). kImages: also write the periodic halo images (the
 // TMA-staged step reads them; the L1 pull wraps instead). kHalo = false: no
-// domain of the launch has a non-periodic side, so with kImages = false there is
-// no halo cell to write and the relaxed values need not go back to the column.
+// side of any domain of the launch has ghosts that the step writes (every side
+// periodic or exchanged), so with kImages = false there is no halo cell to write
+// and the relaxed values need not go back to the column.
 template <int EDF, class S, bool kImages, bool kHalo = true>
 __device__ __forceinline__ unsigned collide_mixed(const DomDev& D, int x, int y, long long c, const float A[12],
                                                   const float B[12], float* smf, int tid,
@@ -665,8 +665,9 @@ __device__ __forceinline__ void step_tile_mixed(const StepArgs& a, int t, float*
   if (st) atomicOr(a.status, st);
 }
 
-// kHalo = false: every domain of the launch is periodic on all sides (launched
-// when StepArgs::halo is 0): no halo writer and no copy of the relaxed values.
+// kHalo = false: every side of every domain of the launch is periodic or
+// exchanged (launched when StepArgs::halo is 0): no halo writer and no copy of
+// the relaxed values.
 template <int EDF, class S, bool kHalo>
 __global__ void __launch_bounds__(kThreads, RLBM_MIXED_MIN_BLOCKS) k_step_mixed(StepArgs a) {
   extern __shared__ float smf[];
