@@ -182,7 +182,7 @@ struct rlbm_ctx {
   int kernel = RLBM_KERNEL_L1;   // mixed step variant (rlbm_select_kernel)
   unsigned long long wait_ns = 0;  // TMA copy-wait limit (0: the default, rlbm_set_wait_limit)
   bool images_stale = false;     // the current copy lacks its periodic halo images (fill_images)
-  int any_halo = 1;              // some domain has a side whose ghosts the step writes
+  int halo = 2;                  // halo work of a step launch (StepArgs::halo)
 };
 
 namespace {
@@ -209,7 +209,7 @@ cudaError_t launch_step(rlbm_ctx* h, int from) {
   a.tmaps = tma ? h->d_tmaps + (size_t)from * per : nullptr;
   a.variant = h->kernel;
   a.wait_ns = h->wait_ns;
-  a.halo = h->any_halo;
+  a.halo = h->halo;
   const int grid = h->grid > 0 ? h->grid : a.ntiles;
   if (h->storage == RLBM_F64) return launch_step_f64(h->edf, a, grid, h->stream);
   return launch_step_mixed(h->storage, h->edf, a, grid, h->stream);
@@ -427,11 +427,11 @@ int rlbm_create(const rlbm_config* c, rlbm_handle* out) {
     delete h;
     return RLBM_E_NOBUFFER;
   }
-  h->any_halo = 0;
+  h->halo = 0;
   for (const rlbm_domain& d : h->doms) {
     h->cells += (long long)d.nx * d.ny;
     for (int b : {d.bc_xlo, d.bc_xhi, d.bc_ylo, d.bc_yhi})
-      if (bc_writes_halo(b)) h->any_halo = 1;
+      if (bc_writes_halo(b)) h->halo = std::max(h->halo, b == RLBM_FIXED_T_WALL ? 1 : 2);
   }
   h->base = static_cast<char*>(c->device_buffer);
   h->d_status = reinterpret_cast<unsigned*>(h->base + h->L.status_off);

@@ -106,7 +106,8 @@ struct StepArgs {
   unsigned* status;       // OR of per-cell status bits
   const void* tmaps;      // TMA load descriptors of fin, one per domain (kTensorMapBytes each), or null
   int variant;            // mixed step kernel (RLBM_KERNEL_*); the FP64 step has one
-  int halo;               // some domain has a side whose ghosts the step writes (bc_writes_halo)
+  int halo;               // halo work of the launch: 0 none (every side periodic or exchanged),
+                          // 1 wall equilibria only, 2 also zero-gradient copies
   unsigned long long wait_ns;  // limit of the TMA variant's copy waits (0: kDefaultWaitNs)
 };
 

@@ -498,18 +498,19 @@ __device__ __forceinline__ void relax_cell(const DomDev& D, const float zr[21], 
 // each direction; stores f* to fout, writes the cell's halo images and returns
 // its status bits. Called by the active lanes of a warp (the lanes of cells
 // inside the domain). kImages: also write the periodic halo images (the
-// TMA-staged step reads them; the L1 pull wraps instead). kHalo = false: no
-// side of any domain of the launch has ghosts that the step writes (every side
-// periodic or exchanged), so with kImages = false there is no halo cell to write
-// and the relaxed values need not go back to the column.
-template <int EDF, class S, bool kImages, bool kHalo = true>
+// TMA-staged step reads them; the L1 pull wraps instead). kHalo, the launch's
+// halo work (StepArgs::halo): 0 none (every side periodic or exchanged), 1 wall
+// equilibria only (every other side a fixed-T wall), 2 also copies (zero-gradient
+// sides). Below 2, with kImages = false, no halo cell copies the cell's relaxed
+// values, so they need not go back to the column.
+template <int EDF, class S, bool kImages, int kHalo = 2>
 __device__ __forceinline__ unsigned collide_mixed(const DomDev& D, int x, int y, long long c, const float A[12],
                                                   const float B[12], float* smf, int tid,
                                                   typename S::T* __restrict__ fout) {
   // a warp with no cell on an edge that has halo cells to write skips the halo
   // writer (uniform per warp)
   const bool edge = kImages ? (x == 0 || x == D.nx - 1 || y == 0 || y == D.ny - 1)
-                            : kHalo && ((x == 0 && bc_writes_halo(D.bc[0])) ||
+                            : kHalo > 0 && ((x == 0 && bc_writes_halo(D.bc[0])) ||
                                         (x == D.nx - 1 && bc_writes_halo(D.bc[1])) ||
                                         (y == 0 && bc_writes_halo(D.bc[2])) ||
                                         (y == D.ny - 1 && bc_writes_halo(D.bc[3])));
@@ -591,7 +592,7 @@ __device__ __forceinline__ unsigned collide_mixed(const DomDev& D, int x, int y,
     float om[12];
 #pragma unroll
     for (int d = 0; d < 12; ++d) om[d] = relax_rate(d, gf, uxf, uyf, itau);
-    if constexpr (!kImages && !kHalo) {
+    if constexpr (!kImages && kHalo < 2) {
       relax_cell<EDF, S, false>(D, zr, zi, om, smf, tid, c, fout);
     } else {
 #if RLBM_MIXED_EDGE_WARPS
@@ -604,7 +605,7 @@ __device__ __forceinline__ unsigned collide_mixed(const DomDev& D, int x, int y,
   } else {
     for (int q = 0; q < 72; ++q) fout[q * kBlkW + c] = S::encf(smf[q * kThreads + tid], D, q % 6);
   }
-  if (kImages || kHalo)
+  if (kImages || kHalo > 0)
     if (edge_warp) write_halo_mixed<EDF, S>(D, x, y, fout, smf + tid, ok, nf, uxf, uyf, gf, st, kImages);
   return st;
 }
@@ -624,7 +625,7 @@ __device__ __forceinline__ void prefetch_tile_l2(const DomDev& D, const Tile& tl
 
 // One tile of the step (32 x 4 cells, or a packed ragged block): pull,
 // collide, store (the thread's cell).
-template <int EDF, class S, bool kHalo>
+template <int EDF, class S, int kHalo>
 __device__ __forceinline__ void step_tile_mixed(const StepArgs& a, int t, float* smf, int tid) {
   const Tile tl = a.tiles[t];
   const DomDev& D = a.doms[tl.dom];
@@ -665,10 +666,9 @@ __device__ __forceinline__ void step_tile_mixed(const StepArgs& a, int t, float*
   if (st) atomicOr(a.status, st);
 }
 
-// kHalo = false: every side of every domain of the launch is periodic or
-// exchanged (launched when StepArgs::halo is 0): no halo writer and no copy of
-// the relaxed values.
-template <int EDF, class S, bool kHalo>
+// kHalo = StepArgs::halo (see collide_mixed): 0 no halo writer, 0 and 1 no copy
+// of the relaxed values into the column.
+template <int EDF, class S, int kHalo>
 __global__ void __launch_bounds__(kThreads, RLBM_MIXED_MIN_BLOCKS) k_step_mixed(StepArgs a) {
   extern __shared__ float smf[];
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
@@ -1091,9 +1091,11 @@ template <class S, int EDF>
 static cudaError_t prepare_mixed_t() {
   cudaError_t e = cudaFuncSetAttribute(k_init_mixed<EDF, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemF);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_step_mixed<EDF, S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemF);
+  e = cudaFuncSetAttribute(k_step_mixed<EDF, S, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemF);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_step_mixed<EDF, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemF);
+  e = cudaFuncSetAttribute(k_step_mixed<EDF, S, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemF);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_step_mixed<EDF, S, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemF);
 }
 
 template <class S>
@@ -1149,19 +1151,20 @@ static cudaError_t step_s(int edf, const StepArgs& a, int grid, cudaStream_t s) 
     return cudaGetLastError();
   }
   const dim3 blk(kTileW, kTileH);
-  if (a.halo) {
-    switch (edf) {
-      case EDF_MJ: k_step_mixed<EDF_MJ, S, true><<<grid, blk, kSmemF, s>>>(a); break;
-      case EDF_FD: k_step_mixed<EDF_FD, S, true><<<grid, blk, kSmemF, s>>>(a); break;
-      default: k_step_mixed<EDF_BE, S, true><<<grid, blk, kSmemF, s>>>(a); break;
-    }
-  } else {
-    switch (edf) {
-      case EDF_MJ: k_step_mixed<EDF_MJ, S, false><<<grid, blk, kSmemF, s>>>(a); break;
-      case EDF_FD: k_step_mixed<EDF_FD, S, false><<<grid, blk, kSmemF, s>>>(a); break;
-      default: k_step_mixed<EDF_BE, S, false><<<grid, blk, kSmemF, s>>>(a); break;
-    }
+#define RLBM_STEP_L1(H)                                                           \
+  switch (edf) {                                                                  \
+    case EDF_MJ: k_step_mixed<EDF_MJ, S, H><<<grid, blk, kSmemF, s>>>(a); break; \
+    case EDF_FD: k_step_mixed<EDF_FD, S, H><<<grid, blk, kSmemF, s>>>(a); break; \
+    default: k_step_mixed<EDF_BE, S, H><<<grid, blk, kSmemF, s>>>(a); break;     \
   }
+  if (a.halo == 0) {
+    RLBM_STEP_L1(0)
+  } else if (a.halo == 1) {
+    RLBM_STEP_L1(1)
+  } else {
+    RLBM_STEP_L1(2)
+  }
+#undef RLBM_STEP_L1
   return cudaGetLastError();
 }
 

@@ -184,7 +184,7 @@ extern "C" int rlbm_step_noalloc(const rlbm_domain* domain, int edf, int nsteps,
     a.tmaps = nullptr;
     a.variant = 0;
     a.wait_ns = 0;
-    a.halo = 1;
+    a.halo = 2;
     e = launch_step_f64(edf, a, P.ntiles, s);
     cur = 1 - cur;
   }
