@@ -131,6 +131,16 @@ typedef struct {
  * tables, a status word and a host-transfer staging area. */
 size_t rlbm_workspace_bytes(const rlbm_config *config);
 
+/* The tile work list a handle of this configuration would walk (host only, no
+ * device work; the paper has no counterpart): packed = 0 the plain list of
+ * 32 x 4 tiles (TMA-staged and FP64 steps, initialisers, read-outs), packed = 1
+ * the list of the mixed L1 step, where each domain's ragged last x block of
+ * w <= 16 cells is one tile per 4 * (32 / w) rows, a warp covering 32 / w rows
+ * of w cells. Writes up to max_tiles quadruples (domain, x0, y0, w) to `out`
+ * (host, int[4 * max_tiles]; may be null) and returns the number of tiles, or
+ * RLBM_E_ARG for an invalid configuration. */
+int rlbm_layout_tiles(const rlbm_config *config, int packed, int *out, int max_tiles);
+
 /* Create a handle over the caller's workspace. Copies the descriptors; uploads
  * the tables; does not initialise populations. *out = NULL on error. */
 int rlbm_create(const rlbm_config *config, rlbm_handle *out);

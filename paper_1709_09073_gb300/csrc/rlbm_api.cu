@@ -410,6 +410,21 @@ size_t rlbm_workspace_bytes(const rlbm_config* c) {
   return L.total;
 }
 
+int rlbm_layout_tiles(const rlbm_config* c, int packed, int* out, int max_tiles) {
+  if (validate(c) || max_tiles < 0) return RLBM_E_ARG;
+  Layout L;
+  make_layout(c, L);
+  const std::vector<Tile>& t = packed ? L.ptiles : L.tiles;
+  if (out)
+    for (size_t i = 0; i < t.size() && (long long)i < max_tiles; ++i) {
+      out[4 * i + 0] = t[i].dom;
+      out[4 * i + 1] = t[i].x0;
+      out[4 * i + 2] = t[i].y0;
+      out[4 * i + 3] = t[i].w;
+    }
+  return (int)t.size();
+}
+
 int rlbm_create(const rlbm_config* c, rlbm_handle* out) {
   if (!out) return RLBM_E_ARG;
   *out = nullptr;

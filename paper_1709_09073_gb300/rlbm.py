@@ -30,7 +30,8 @@ EXPORTS = ["rlbm_workspace_bytes", "rlbm_create", "rlbm_init", "rlbm_step", "rlb
            "rlbm_get_populations", "rlbm_set_populations", "rlbm_tune", "rlbm_sync_status",
            "rlbm_destroy", "rlbm_status_string", "rlbm_last_step_info", "rlbm_step_noalloc", "rlbm_diagnostics",
            "rlbm_select_kernel", "rlbm_edge_row_bytes", "rlbm_pack_edge_rows", "rlbm_unpack_ghost_rows",
-           "rlbm_pipe_peaks", "rlbm_set_wait_limit", "rlbm_init_all", "rlbm_moments_all", "rlbm_set_grid"]
+           "rlbm_pipe_peaks", "rlbm_set_wait_limit", "rlbm_init_all", "rlbm_moments_all", "rlbm_set_grid",
+           "rlbm_layout_tiles"]
 
 
 class rlbm_domain(ctypes.Structure):
@@ -68,6 +69,8 @@ def load(path=None):
     L = ctypes.CDLL(p)
     L.rlbm_workspace_bytes.argtypes = [ctypes.POINTER(rlbm_config)]
     L.rlbm_workspace_bytes.restype = ctypes.c_size_t
+    L.rlbm_layout_tiles.argtypes = [ctypes.POINTER(rlbm_config), ctypes.c_int, ctypes.c_void_p, ctypes.c_int]
+    L.rlbm_layout_tiles.restype = ctypes.c_int
     L.rlbm_create.argtypes = [ctypes.POINTER(rlbm_config), ctypes.POINTER(_H)]
     L.rlbm_init.argtypes = [_H, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
@@ -120,6 +123,17 @@ def rlbm_workspace_bytes(specs, edf, storage, order=5):
     doms = make_domains(specs)
     cfg = rlbm_config(len(specs), doms, edf, storage, order, None, 0, None)
     return load().rlbm_workspace_bytes(ctypes.byref(cfg))
+
+
+def rlbm_layout_tiles(specs, edf, storage, packed):
+    """The tile work list (rows of domain, x0, y0, w) a handle of these domains
+    would walk: the plain 32 x 4 list, or the mixed L1 step's packed one."""
+    doms = make_domains(specs)
+    cfg = rlbm_config(len(specs), doms, edf, storage, 5, None, 0, None)
+    n = _check(load().rlbm_layout_tiles(ctypes.byref(cfg), int(packed), None, 0))
+    out = np.zeros((max(n, 1), 4), dtype=np.int32)
+    _check(load().rlbm_layout_tiles(ctypes.byref(cfg), int(packed), out.ctypes.data_as(ctypes.c_void_p), n))
+    return out[:n]
 
 
 def _ptr(x):
